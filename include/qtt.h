@@ -1,0 +1,234 @@
+/*
+ * qtt.h -- C ABI of the GB300 QTT linear-algebra engine for 2D plane-stress
+ * elasticity (low-rank QTT finite elements on Z-ordered Q1 patch meshes).
+ *
+ * Layout conventions (Section 4 of the paper; readings fixed by this project)
+ * ---------------------------------------------------------------------------
+ *  - A QTT vector (MPS) with d cores has cores T_k of shape
+ *    (r_{k-1}, n_k, r_k), r_0 = r_d = 1.  A QTT matrix (MPO) has cores A_k of
+ *    shape (r_{k-1}, n_k, m_k, r_k): row mode i, column mode j, read as the
+ *    long index i + n_k j (the paper's remark on MPO cores).
+ *  - Every core is stored COLUMN-MAJOR: element (a, i, b) of an MPS core sits
+ *    at a + r_{k-1} (i + n_k b); element (a, i, j, b) of an MPO core at
+ *    a + r_{k-1} (i + n_k (j + m_k b)).
+ *  - The first core carries the least significant index digit (binary
+ *    quantisation of Section 4): full[i_1 + n_1 i_2 + n_1 n_2 i_3 + ...] =
+ *    T_1[:, i_1, :] T_2[:, i_2, :] ... T_d[:, i_d, :].
+ *  - The elasticity layout of a problem with q patches and n = 2^L nodes per
+ *    patch side has D = L + [q > 1] + 1 cores: L position cores of mode 4
+ *    with mode index i_l + 2 j_l (the Z-order bit pair of level l, Section
+ *    3.2), then a patch core of mode q (omitted for q = 1), then a component
+ *    core of mode 2 (x, y) -- the block Kronecker assembly of Section 3.7
+ *    places the component outermost.
+ *
+ * Ownership and streams
+ * ---------------------
+ *  - qtt_tensor objects are opaque, created by the library, hold their cores
+ *    in device memory, and are released with qtt_free.
+ *  - Entry points are stream-ordered on the cudaStream_t passed as `stream`
+ *    (NULL = legacy default stream).  Entry points whose results decide a
+ *    rank (rounding, solving) synchronise that stream before returning.
+ *  - Caller buffers (`dst` of qtt_to_full, host core arrays) are owned by the
+ *    caller and must not be freed before the call's stream work completes.
+ *
+ * Errors
+ * ------
+ *  Every function returns QTT_OK (0) or a negative QTT_E* code; nothing is
+ *  thrown across the ABI.  qtt_last_error() returns a thread-local message
+ *  describing the most recent failure on the calling thread.
+ */
+#ifndef QTT_H_
+#define QTT_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QTT_OK 0
+#define QTT_EINVAL (-1)     /* invalid argument (shape, mode size, pointer) */
+#define QTT_ENOMEM (-2)     /* device allocation failed */
+#define QTT_ECUDA (-3)      /* a CUDA runtime call or kernel launch failed */
+#define QTT_ENOCONV (-4)    /* solver stopped at max_sweeps above tolerance */
+#define QTT_ETIMEOUT (-5)   /* a bounded device-side wait gave up */
+#define QTT_ERANKCAP (-6)   /* a rank would exceed max_rank at tolerance */
+
+#define QTT_F64 0           /* storage and arithmetic in double */
+#define QTT_F32 1           /* storage and arithmetic in float */
+#define QTT_MIXED 2         /* solve: FP32 inner AMEn + FP64 refinement */
+
+#define QTT_ORDER_Z_BLOCK 0    /* native QTT order: z-ordered position, patch, component */
+#define QTT_ORDER_CANONICAL 1  /* per patch, interleaved components 2 (i + n j) + c */
+
+#define QTT_MAX_CORES 40
+
+typedef struct qtt_tensor qtt_tensor;
+
+/* ------------------------------------------------------------------------ */
+/* Tensor objects                                                            */
+/* ------------------------------------------------------------------------ */
+
+/* Create a tensor from host cores.  d cores; n[k] row mode sizes; m[k] column
+ * mode sizes (NULL or all 1 for an MPS); ranks[0..d], ranks[0] = ranks[d] =
+ * 1; prec QTT_F64 (cores are double*) or QTT_F32 (float*).  host_cores[k]
+ * points to ranks[k] n[k] m[k] ranks[k+1] column-major elements; they are
+ * copied, so the caller keeps ownership.  Returns QTT_EINVAL on bad shapes. */
+int qtt_tensor_create(int d, const int* n, const int* m, const int* ranks, int prec,
+                      const void* const* host_cores, qtt_tensor** out);
+
+/* Query shape: any pointer may be NULL.  n, m have d entries; ranks d + 1. */
+int qtt_tensor_info(const qtt_tensor* t, int* d, int* n, int* m, int* ranks, int* prec);
+
+/* Copy the cores back to host buffers host_dst[k] (sized as in create). */
+int qtt_tensor_get_cores(const qtt_tensor* t, void* const* host_dst);
+
+/* Device pointer of core k (column-major), for zero-copy access. */
+int qtt_tensor_core_ptr(const qtt_tensor* t, int k, void** dev_ptr);
+
+/* Deep copy, optionally converting precision (QTT_F64 / QTT_F32). */
+int qtt_tensor_copy(const qtt_tensor* src, int prec, qtt_tensor** out, void* stream);
+
+void qtt_free(qtt_tensor* t);
+
+const char* qtt_last_error(void);
+
+/* ------------------------------------------------------------------------ */
+/* Problem description and assembly (Algorithm 1)                           */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int L;                     /* levels: n = 2^L nodes per patch side (Section 3.2) */
+  int q;                     /* number of unit-square patches (Section 3.1) */
+  const int* patch_xy;       /* 2q ints: integer offset (ox, oy) of each patch */
+  double E, nu;              /* Young's modulus, Poisson ratio; plane stress (Eq. Cmat) */
+  const int* bc;             /* 4q ints: side flags (left, right, bottom, top) per
+                                patch; bit 1 = u_x fixed, bit 2 = u_y fixed (Section 3.8) */
+  int n_body;                /* separable body-force terms f_c = a g(x) h(y) */
+  const int* body_terms;     /* 3 n_body ints: (component, xkind, ykind);
+                                kinds 0..4 = 1, t, sin(pi t), cos(pi t), t^2 */
+  const double* body_coef;   /* n_body coefficients a */
+  int n_trac;                /* constant edge tractions */
+  const int* trac_where;     /* 2 n_trac ints: (patch, side) */
+  const double* trac_val;    /* 2 n_trac doubles: (t_x, t_y) */
+  double gamma;              /* concatenation penalty (Section 3.6); 0 = mean
+                                diagonal of K_xx of one patch */
+  double tol;                /* relative rounding tolerance of the assembled
+                                K and f (0 = 1e-13) */
+} qtt_problem;
+
+/* Assemble the stiffness MPO K and load MPS f of a problem in FP64 on the
+ * device (Algorithm 1: 1D factors -> z-kron -> patch concatenation with
+ * connectivity Pi^(mp) and penalty gamma -> component blocks -> Dirichlet
+ * masks K <- M K M + (I - M), f <- M f -> rounding).  Patches are unit
+ * squares at integer offsets; two patches share an edge or a corner exactly
+ * when their offsets differ by one in one or both directions.  Creates *K and
+ * *f (caller frees with qtt_free).  Errors: QTT_EINVAL for L < 1, L > 18,
+ * q < 1, q > 16, bad flags or kinds. */
+int qtt_assemble_stiffness(const qtt_problem* p, qtt_tensor** K, qtt_tensor** f, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Core operations                                                           */
+/* ------------------------------------------------------------------------ */
+
+/* y = A x, MPO times MPS, core by core:
+ *   Y_k[(a, g), i, (b, e)] = sum_j A_k[a, i, j, b] X_k[g, j, e]
+ * (the paper's "algebraic matrix-vector operations", Section 4).  The output
+ * rank index is (a, g) with a fastest.  If tol > 0 the product is rounded to
+ * relative accuracy tol (qtt_round), else returned with ranks R_k r_k.
+ * A and x must share precision and mode sizes (A's column modes = x's modes).
+ * Creates *y. */
+int qtt_matvec(const qtt_tensor* A, const qtt_tensor* x, double tol, int max_rank,
+               qtt_tensor** y, void* stream);
+
+/* In-place TT rounding (Oseledets 2011, Alg. 2, cited in Section 1): a
+ * left-to-right Householder QR sweep, then a right-to-left truncated-SVD
+ * sweep; every bond keeps the smallest rank whose discarded singular values
+ * have 2-norm <= tol ||x|| / sqrt(d - 1).  Works for MPS and MPO (mode pairs
+ * read as one long index).  max_rank <= 0 means unlimited; if the tolerance
+ * needs more than max_rank the bond is cut at max_rank and QTT_ERANKCAP is
+ * returned (the tensor is still valid).  Synchronises the stream. */
+int qtt_round(qtt_tensor* x, double tol, int max_rank, void* stream);
+
+/* z = alpha x + beta y (ranks add; no rounding).  Creates *z. */
+int qtt_axpby(double alpha, const qtt_tensor* x, double beta, const qtt_tensor* y,
+              qtt_tensor** z, void* stream);
+
+/* Frobenius norm by left orthogonalisation (stable for small differences:
+ * the absolute error is of order eps times the norms of the summands).
+ * Writes *out on the host; synchronises the stream. */
+int qtt_norm(const qtt_tensor* x, double* out, void* stream);
+
+/* Expand an MPS to a full vector (Section 4 entry-wise formula).  dst is a
+ * DEVICE pointer with room for n_elems elements of the tensor's precision;
+ * n_elems must equal the product of the mode sizes.  ordering:
+ *   QTT_ORDER_Z_BLOCK    -- the native QTT index (z-ordered position, then
+ *                           patch, then component);
+ *   QTT_ORDER_CANONICAL  -- patch-major blocks, inside a patch the DOF pair
+ *                           N_ij = (2 L_ij, 2 L_ij + 1) (0-based) with the
+ *                           canonical node number L_ij = i + 2^L j (Section 3.2);
+ *                           needs the elasticity layout (L, q inferred from
+ *                           the cores: L mode-4 cores, optional mode-q core,
+ *                           final mode-2 core).
+ * For an MPO, n_elems must equal (prod n)(prod m) and only
+ * QTT_ORDER_Z_BLOCK is accepted (dense column-major matrix). */
+int qtt_to_full(const qtt_tensor* x, void* dst, size_t n_elems, int ordering, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Solver (AMEn, cited by the paper for K u = f)                             */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  double tol;             /* target: max local relative residual per sweep (and
+                             the FP64 global relative residual for QTT_MIXED) */
+  int max_rank;           /* cap on solution ranks (<= 0: 512) */
+  int kick_rank;          /* residual-proxy rank rho used for enrichment (<= 0: 4) */
+  int max_sweeps;         /* per AMEn run (<= 0: 30) */
+  int local_direct_max;   /* local systems up to this size use dense LU (<= 0: 2048) */
+  int local_restart;      /* GMRES restart length for larger local systems (<= 0: 40) */
+  int local_max_cycles;   /* GMRES restart cycles per local solve (<= 0: 8) */
+  int precision;          /* QTT_F64, QTT_F32 or QTT_MIXED */
+  int refine_max;         /* QTT_MIXED: maximum refinement steps (<= 0: 6) */
+  double inner_tol;       /* QTT_MIXED: tolerance of each FP32 inner solve (<= 0: 1e-5) */
+  int verbose;            /* print per-sweep progress to stderr */
+} qtt_solve_opts;
+
+typedef struct {
+  int status;             /* QTT_OK or the returned error code */
+  int sweeps;             /* total AMEn sweeps (all inner solves) */
+  int local_solves;       /* local systems solved */
+  int local_iters;        /* GMRES iterations over all local solves */
+  int max_rank;           /* largest solution rank */
+  int refinements;        /* QTT_MIXED outer steps */
+  double max_local_res;   /* last sweep's maximum local relative residual */
+  double rel_residual;    /* FP64 ||f - K u|| / ||f|| (computed when tol > 0) */
+  double erank;           /* effective rank of the solution (Section 4) */
+} qtt_solve_info;
+
+/* Solve K u = f.  x0: initial guess (NULL = rank-1 constant); z0: initial
+ * residual proxy of rank kick_rank (NULL = a fixed deterministic proxy).  One-
+ * directional AMEn sweeps: right-orthogonalise x and z, then for every core
+ * build the local Galerkin system from the left/right interface tensors,
+ * record its relative residual, solve it (dense LU or restarted GMRES), SVD-
+ * truncate it at the smallest rank whose local residual stays <= tol /
+ * sqrt(D), enrich the basis with the residual projected on the proxy's
+ * interfaces, and update the interfaces; stop when the sweep's maximum local
+ * residual is <= tol.  With QTT_MIXED the sweeps run in FP32 on an FP32 copy
+ * of K and the residual f - K u is formed and rounded in FP64 between
+ * solves (iterative refinement).  Creates *x; info may be NULL.  Returns
+ * QTT_ENOCONV (with *x valid) if max_sweeps / refine_max run out. */
+int qtt_solve(const qtt_tensor* K, const qtt_tensor* f, const qtt_tensor* x0,
+              const qtt_tensor* z0, const qtt_solve_opts* opts, qtt_tensor** x,
+              qtt_solve_info* info, void* stream);
+
+/* FP64 relative residual ||f - K u|| / ||f||: the product K u and the sum are
+ * formed in QTT and normed by orthogonalisation (no rounding).  Writes *out
+ * on the host; synchronises the stream. */
+int qtt_residual(const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* f,
+                 double* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif  /* QTT_H_ */

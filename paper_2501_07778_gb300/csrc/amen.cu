@@ -1,0 +1,666 @@
+// qtt_solve: one-site AMEn with residual-based enrichment (Dolgov &
+// Savostyanov 2014, the solver the paper uses for K u = f), restated for
+// this engine:
+//   right-orthogonalise x and the residual proxy z; build right interfaces
+//   Phi_R(x,K,x), Psi_R(x,f), Phi_R(z,K,x), Psi_R(z,f);
+//   for k = 1..D: local Galerkin system B_k = Phi_L K_k Phi_R, local rhs g_k;
+//     record ||B_k x_k - g_k|| / ||g_k||; solve (dense LU or restarted
+//     GMRES); truncate the left unfolding by SVD at the smallest rank whose
+//     local residual stays within tol / sqrt(D); new z core = orth of the
+//     residual projected on z's interfaces; enrich [U, residual projected on
+//     x's left and z's right interfaces], orthogonalise, push the remainder
+//     into core k+1; update the left interfaces;
+//   stop when the sweep's largest local residual is <= tol.
+// Mixed precision (QTT_MIXED): the sweeps run in FP32 and the outer loop
+// forms r = f - K u by the QTT matvec in FP64, rounds it in FP64, solves
+// K d = r in FP32 and updates u <- round64(u + d).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <vector>
+
+#include "common.cuh"
+#include "tt_ops.cuh"
+
+namespace qtt {
+namespace {
+
+using Tptr = std::unique_ptr<qtt_tensor, void (*)(qtt_tensor*)>;
+Tptr own(qtt_tensor* t) { return Tptr(t, tensor_free); }
+
+inline int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 4864)); }
+
+// growable device buffer
+template <typename T>
+struct DBuf {
+  T* p = nullptr;
+  size_t cap = 0;
+  cudaStream_t s = nullptr;
+  void ensure(size_t n, cudaStream_t st) {
+    s = st;
+    if (n <= cap) return;
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+    size_t c = std::max<size_t>(n, cap * 3 / 2);
+    cudaError_t e = cudaMallocAsync(&p, c * sizeof(T), s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw QttError(QTT_ENOMEM, "solver buffer allocation failed");
+    }
+    cap = c;
+  }
+  ~DBuf() {
+    if (p) cudaFreeAsync(p, s);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// small device helpers
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void scale_by_device_kernel(T* v, const T* src, int n, const double* nrm2, double* hout) {
+  double h = sqrt(*nrm2);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && hout) *hout = h;
+  double inv = h > 0 ? 1.0 / h : 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = (T)((double)src[i] * inv);
+}
+
+// Givens least squares for min || beta e1 - H y ||, H (m+1) x m (ld m+1),
+// single thread block; writes y (m) and the residual estimate
+__global__ void gmres_lsq_kernel(const double* H, int m, double beta, double* y, double* res) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double R[65 * 64];
+  double g[65];
+  const int ld = m + 1;
+  for (int j = 0; j < m; ++j)
+    for (int i = 0; i <= m; ++i) R[i + ld * j] = H[i + ld * j];
+  for (int i = 0; i <= m; ++i) g[i] = 0.0;
+  g[0] = beta;
+  for (int j = 0; j < m; ++j) {
+    double a = R[j + ld * j], b = R[j + 1 + ld * j];
+    double r = sqrt(a * a + b * b);
+    double c = r > 0 ? a / r : 1.0, s = r > 0 ? b / r : 0.0;
+    for (int k = j; k < m; ++k) {
+      double x1 = R[j + ld * k], x2 = R[j + 1 + ld * k];
+      R[j + ld * k] = c * x1 + s * x2;
+      R[j + 1 + ld * k] = -s * x1 + c * x2;
+    }
+    double g1 = g[j], g2 = g[j + 1];
+    g[j] = c * g1 + s * g2;
+    g[j + 1] = -s * g1 + c * g2;
+  }
+  for (int i = m - 1; i >= 0; --i) {
+    double v = g[i];
+    for (int k = i + 1; k < m; ++k) v -= R[i + ld * k] * y[k];
+    double d = R[i + ld * i];
+    y[i] = d != 0.0 ? v / d : 0.0;
+  }
+  *res = fabs(g[m]);
+}
+
+template <typename T>
+__global__ void store_col_kernel(double* H, int ldh, int j, const T* h, int len, const double* hlast) {
+  int i = threadIdx.x + blockIdx.x * blockDim.x;
+  if (i < len) H[i + (long long)ldh * j] = (double)h[i];
+  if (i == 0 && hlast) H[len + (long long)ldh * j] = *hlast;
+}
+
+template <typename T>
+__global__ void to_T_kernel(const double* src, T* dst, int n) {
+  int i = threadIdx.x + blockIdx.x * blockDim.x;
+  if (i < n) dst[i] = (T)src[i];
+}
+
+template <typename T>
+__global__ void scale_rows_kernel(int rows, int cols, const T* A, int lda, const T* S, T* B, int ldb) {
+  long long total = (long long)rows * cols;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(t % rows), j = (int)(t / rows);
+    B[i + (long long)j * ldb] = A[i + (long long)j * lda] * S[i];
+  }
+}
+
+// deterministic residual proxy when none is given: smooth sign-varying values
+template <typename T>
+__global__ void proxy_kernel(T* c, long long n, int k) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    c[i] = (T)sin(0.7 + 1.3 * (double)i + 2.1 * (double)k + 0.37 * (double)(i * i % 97));
+}
+
+// ---------------------------------------------------------------------------
+// the solver
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Amen {
+  cudaStream_t s;
+  Arena& ar;
+  const qtt_tensor* A;
+  const qtt_tensor* y;
+  qtt_tensor* x;
+  qtt_tensor* z;
+  int D;
+  double tol;
+  int max_rank, kick, max_sweeps, ndir, restart, cycles, verbose;
+  // interfaces: PhiR[k] (bond k), k = 0..D
+  std::vector<DBuf<T>> XAX_R, XY_R, ZAX_R, ZY_R;
+  DBuf<T> XAX_L, XY_L, ZAX_L, ZY_L, XAX_Ln, XY_Ln, ZAX_Ln, ZY_Ln;
+  double* dscal;   // device scratch scalars
+  qtt_solve_info* info;
+
+  Amen(cudaStream_t st, Arena& a) : s(st), ar(a) {}
+
+  int rA(int k) const { return A->r[k]; }
+  int ry(int k) const { return y->r[k]; }
+
+  double host_norm(const T* v, size_t n) {
+    sumsq<T>(s, v, n, dscal);
+    double h;
+    QTT_CUDA(cudaMemcpyAsync(&h, dscal, sizeof(double), cudaMemcpyDeviceToHost, s));
+    QTT_CUDA(cudaStreamSynchronize(s));
+    return std::sqrt(h);
+  }
+
+  // (B x)[a,i,b] with B = PhiL (ra,R0,rc) K_k PhiR (rb,R1,rd), x (rc, n, rd)
+  void local_apply(const T* PhiL, int ra, int rc, int k, const T* PhiR, int rb, int rd, const T* xk, T* out, Arena& sc) {
+    const int n = A->n[k], R0 = rA(k), R1 = rA(k + 1);
+    int dx[3] = {rc, n, rd}, dR[3] = {rb, R1, rd};
+    T* t1 = sc.alloc<T>((size_t)rc * n * rb * R1);
+    einsum<T>(s, sc, "cjd,bBd->cjbB", xk, dx, PhiR, dR, t1);
+    int d1[4] = {rc, n, rb, R1}, dA[4] = {R0, n, n, R1};
+    T* t2 = sc.alloc<T>((size_t)rc * rb * R0 * n);
+    einsum<T>(s, sc, "cjbB,AijB->cbAi", t1, d1, (const T*)A->core[k], dA, t2);
+    int dL[3] = {ra, R0, rc}, d2[4] = {rc, rb, R0, n};
+    einsum<T>(s, sc, "aAc,cbAi->aib", PhiL, dL, t2, d2, out);
+  }
+
+  // g[a,i,b] = PsiL (ra, ryl) y_k (ryl, n, ryr) PsiR (rb, ryr)
+  void local_rhs(const T* PsiL, int ra, int k, const T* PsiR, int rb, T* out, Arena& sc) {
+    const int n = y->n[k], r0 = ry(k), r1 = ry(k + 1);
+    int dL[2] = {ra, r0}, dy[3] = {r0, n, r1};
+    T* t = sc.alloc<T>((size_t)ra * n * r1);
+    einsum<T>(s, sc, "ac,cid->aid", PsiL, dL, (const T*)y->core[k], dy, t);
+    int dt[3] = {ra, n, r1}, dR[2] = {rb, r1};
+    einsum<T>(s, sc, "aid,bd->aib", t, dt, PsiR, dR, out);
+  }
+
+  // right interface of bond k from bond k+1: Phi[a,A,c] = X[a,i,b] K[A,i,j,B] Y[c,j,d] Phi'[b,B,d]
+  void right_XAX(const qtt_tensor* X, const qtt_tensor* Y, int k, const T* Phin, T* out, Arena& sc) {
+    const int n = A->n[k], R0 = rA(k), R1 = rA(k + 1);
+    const int xa = X->r[k], xb = X->r[k + 1], yc = Y->r[k], yd = Y->r[k + 1];
+    int dY[3] = {yc, n, yd}, dP[3] = {xb, R1, yd};
+    T* t1 = sc.alloc<T>((size_t)yc * n * xb * R1);
+    einsum<T>(s, sc, "cjd,bBd->cjbB", (const T*)Y->core[k], dY, Phin, dP, t1);
+    int d1[4] = {yc, n, xb, R1}, dA[4] = {R0, n, n, R1};
+    T* t2 = sc.alloc<T>((size_t)yc * xb * R0 * n);
+    einsum<T>(s, sc, "cjbB,AijB->cbAi", t1, d1, (const T*)A->core[k], dA, t2);
+    int dX[3] = {xa, n, xb}, d2[4] = {yc, xb, R0, n};
+    einsum<T>(s, sc, "aib,cbAi->aAc", (const T*)X->core[k], dX, t2, d2, out);
+  }
+
+  // left: Phi'[b,B,d] = Phi[a,A,c] X[a,i,b] K[A,i,j,B] Y[c,j,d]
+  void left_XAX(const qtt_tensor* X, const qtt_tensor* Y, int k, const T* Phi, T* out, Arena& sc) {
+    const int n = A->n[k], R0 = rA(k), R1 = rA(k + 1);
+    const int xa = X->r[k], xb = X->r[k + 1], yc = Y->r[k], yd = Y->r[k + 1];
+    int dP[3] = {xa, R0, yc}, dX[3] = {xa, n, xb};
+    T* t1 = sc.alloc<T>((size_t)R0 * yc * n * xb);
+    einsum<T>(s, sc, "aAc,aib->Acib", Phi, dP, (const T*)X->core[k], dX, t1);
+    int d1[4] = {R0, yc, n, xb}, dA[4] = {R0, n, n, R1};
+    T* t2 = sc.alloc<T>((size_t)yc * xb * n * R1);
+    einsum<T>(s, sc, "Acib,AijB->cbjB", t1, d1, (const T*)A->core[k], dA, t2);
+    int d2[4] = {yc, xb, n, R1}, dY[3] = {yc, n, yd};
+    einsum<T>(s, sc, "cbjB,cjd->bBd", t2, d2, (const T*)Y->core[k], dY, out);
+  }
+
+  // Psi[a,c] = X[a,i,b] y[c,i,d] Psi'[b,d]
+  void right_XY(const qtt_tensor* X, int k, const T* Psin, T* out, Arena& sc) {
+    const int n = y->n[k], xa = X->r[k], xb = X->r[k + 1], c0 = ry(k), c1 = ry(k + 1);
+    int dy[3] = {c0, n, c1}, dP[2] = {xb, c1};
+    T* t = sc.alloc<T>((size_t)c0 * n * xb);
+    einsum<T>(s, sc, "cid,bd->cib", (const T*)y->core[k], dy, Psin, dP, t);
+    int dX[3] = {xa, n, xb}, dt[3] = {c0, n, xb};
+    einsum<T>(s, sc, "aib,cib->ac", (const T*)X->core[k], dX, t, dt, out);
+  }
+
+  void left_XY(const qtt_tensor* X, int k, const T* Psi, T* out, Arena& sc) {
+    const int n = y->n[k], xa = X->r[k], xb = X->r[k + 1], c0 = ry(k), c1 = ry(k + 1);
+    int dP[2] = {xa, c0}, dX[3] = {xa, n, xb};
+    T* t = sc.alloc<T>((size_t)c0 * n * xb);
+    einsum<T>(s, sc, "ac,aib->cib", Psi, dP, (const T*)X->core[k], dX, t);
+    int dt[3] = {c0, n, xb}, dy[3] = {c0, n, c1};
+    einsum<T>(s, sc, "cib,cid->bd", t, dt, (const T*)y->core[k], dy, out);
+  }
+
+  void set_one(DBuf<T>& b) {
+    b.ensure(1, s);
+    fill<T>(s, b.p, 1, T(1));
+  }
+
+  void build_right_interfaces() {
+    XAX_R.resize(D + 1);
+    XY_R.resize(D + 1);
+    ZAX_R.resize(D + 1);
+    ZY_R.resize(D + 1);
+    set_one(XAX_R[D]);
+    set_one(XY_R[D]);
+    set_one(ZAX_R[D]);
+    set_one(ZY_R[D]);
+    for (int k = D - 1; k >= 1; --k) {
+      Arena sc(s);
+      XAX_R[k].ensure((size_t)x->r[k] * rA(k) * x->r[k], s);
+      right_XAX(x, x, k, XAX_R[k + 1].p, XAX_R[k].p, sc);
+      XY_R[k].ensure((size_t)x->r[k] * ry(k), s);
+      right_XY(x, k, XY_R[k + 1].p, XY_R[k].p, sc);
+      ZAX_R[k].ensure((size_t)z->r[k] * rA(k) * x->r[k], s);
+      right_XAX(z, x, k, ZAX_R[k + 1].p, ZAX_R[k].p, sc);
+      ZY_R[k].ensure((size_t)z->r[k] * ry(k), s);
+      right_XY(z, k, ZY_R[k + 1].p, ZY_R[k].p, sc);
+    }
+  }
+
+  // restarted GMRES on the local operator; x holds the initial guess and
+  // receives the solution; returns the final relative residual estimate
+  double gmres(int k, const T* PhiL, int r0, const T* PhiR, int r1, const T* g, double gn, T* xk, double rtol) {
+    const int n = A->n[k];
+    const int N = r0 * n * r1;
+    const int m = std::min(restart, N);
+    Arena sc(s);
+    T* V = sc.alloc<T>((size_t)N * (m + 1));
+    T* w = sc.alloc<T>(N);
+    T* hcol = sc.alloc<T>(m + 1);
+    T* hcol2 = sc.alloc<T>(m + 1);
+    double* H = sc.alloc<double>((size_t)(m + 1) * m);
+    double* yv = sc.alloc<double>(m);
+    T* yT = sc.alloc<T>(m);
+    double* dres = sc.alloc<double>(1);
+    double* hlast = sc.alloc<double>(1);
+    double rel = 1.0;
+    for (int cyc = 0; cyc < cycles; ++cyc) {
+      Arena it(s);
+      // r0 = g - B x
+      local_apply(PhiL, r0, r0, k, PhiR, r1, r1, xk, w, it);
+      axpby<T>(s, N, T(1), g, T(-1), w);        // w = g - Bx
+      double beta = host_norm(w, N);
+      rel = gn > 0 ? beta / gn : beta;
+      if (rel <= rtol || beta == 0.0) break;
+      QTT_CUDA(cudaMemsetAsync(H, 0, sizeof(double) * (m + 1) * m, s));
+      sumsq<T>(s, w, N, dscal);
+      scale_by_device_kernel<T><<<grid_for(N), 256, 0, s>>>(V, w, N, dscal, nullptr);
+      QTT_CHECK_LAUNCH();
+      for (int j = 0; j < m; ++j) {
+        Arena ij(s);
+        local_apply(PhiL, r0, r0, k, PhiR, r1, r1, V + (size_t)N * j, w, ij);
+        // classical Gram-Schmidt, twice
+        gemm<T>(s, true, false, j + 1, 1, N, T(1), V, N, 0, w, N, 0, T(0), hcol, j + 1, 0);
+        gemm<T>(s, false, false, N, 1, j + 1, T(-1), V, N, 0, hcol, j + 1, 0, T(1), w, N, 0);
+        gemm<T>(s, true, false, j + 1, 1, N, T(1), V, N, 0, w, N, 0, T(0), hcol2, j + 1, 0);
+        gemm<T>(s, false, false, N, 1, j + 1, T(-1), V, N, 0, hcol2, j + 1, 0, T(1), w, N, 0);
+        axpby<T>(s, j + 1, T(1), hcol2, T(1), hcol);
+        sumsq<T>(s, w, N, dscal);
+        scale_by_device_kernel<T><<<grid_for(N), 256, 0, s>>>(V + (size_t)N * (j + 1), w, N, dscal, hlast);
+        QTT_CHECK_LAUNCH();
+        store_col_kernel<T><<<(m + 128) / 128, 128, 0, s>>>(H, m + 1, j, hcol, j + 1, hlast);
+        QTT_CHECK_LAUNCH();
+      }
+      gmres_lsq_kernel<<<1, 1, 0, s>>>(H, m, beta, yv, dres);
+      QTT_CHECK_LAUNCH();
+      to_T_kernel<T><<<(m + 127) / 128, 128, 0, s>>>(yv, yT, m);
+      QTT_CHECK_LAUNCH();
+      gemm<T>(s, false, false, N, 1, m, T(1), V, N, 0, yT, m, 0, T(1), xk, N, 0);
+      if (info) info->local_iters += m;
+    }
+    return rel;
+  }
+
+  double local_residual(int k, const T* PhiL, int r0, const T* PhiR, int r1, const T* g, double gn, const T* xk) {
+    const int N = r0 * A->n[k] * r1;
+    Arena sc(s);
+    T* w = sc.alloc<T>(N);
+    local_apply(PhiL, r0, r0, k, PhiR, r1, r1, xk, w, sc);
+    axpby<T>(s, N, T(-1), g, T(1), w);
+    double rn = host_norm(w, N);
+    return gn > 0 ? rn / gn : rn;
+  }
+
+  void ensure_core(qtt_tensor* t, int k, size_t elems) { tensor_reserve(t, k, elems, s); }
+
+  int run() {
+    const double delta = tol / std::sqrt((double)D);
+    int status = QTT_ENOCONV;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+      {
+        Arena sc(s);
+        right_orthogonalize<T>(s, sc, x, 0);
+        right_orthogonalize<T>(s, sc, z, 0);
+      }
+      build_right_interfaces();
+      set_one(XAX_L);
+      set_one(XY_L);
+      set_one(ZAX_L);
+      set_one(ZY_L);
+      double max_res = 0.0;
+      for (int k = 0; k < D; ++k) {
+        Arena sc(s);
+        const int r0 = x->r[k], r1 = x->r[k + 1], n = A->n[k];
+        const int N = r0 * n * r1;
+        const T* PhiR = XAX_R[k + 1].p;
+        T* g = sc.alloc<T>(N);
+        local_rhs(XY_L.p, r0, k, XY_R[k + 1].p, r1, g, sc);
+        const double gn = host_norm(g, N);
+        T* xk = (T*)x->core[k];
+        const double res = local_residual(k, XAX_L.p, r0, PhiR, r1, g, gn, xk);
+        max_res = std::max(max_res, res);
+        // local solve
+        T* sol = sc.alloc<T>(N);
+        if (N <= ndir) {
+          T* Bm = sc.alloc<T>((size_t)N * N);
+          const int R0 = rA(k), R1 = rA(k + 1);
+          int dL[3] = {r0, R0, r0}, dA[4] = {R0, n, n, R1};
+          T* t = sc.alloc<T>((size_t)r0 * r0 * n * n * R1);
+          einsum<T>(s, sc, "aAc,AijB->acijB", XAX_L.p, dL, (const T*)A->core[k], dA, t);
+          int dt[5] = {r0, r0, n, n, R1}, dR[3] = {r1, R1, r1};
+          einsum<T>(s, sc, "acijB,bBd->aibcjd", t, dt, PhiR, dR, Bm);
+          QTT_CUDA(cudaMemcpyAsync(sol, g, sizeof(T) * N, cudaMemcpyDeviceToDevice, s));
+          int* dinfo = sc.alloc<int>(1);
+          lu_solve<T>(s, sc, N, Bm, N, sol, N, 1, dinfo);
+        } else {
+          QTT_CUDA(cudaMemcpyAsync(sol, xk, sizeof(T) * N, cudaMemcpyDeviceToDevice, s));
+          gmres(k, XAX_L.p, r0, PhiR, r1, g, gn, sol, delta);
+        }
+        if (info) info->local_solves += 1;
+        if (k == D - 1) {
+          QTT_CUDA(cudaMemcpyAsync(xk, sol, sizeof(T) * N, cudaMemcpyDeviceToDevice, s));
+          break;
+        }
+        const double res_sol = local_residual(k, XAX_L.p, r0, PhiR, r1, g, gn, sol);
+        // SVD of the left unfolding (r0 n) x r1
+        const int rows = r0 * n, kk = std::min(rows, r1);
+        T* Acp = sc.alloc<T>(N);
+        QTT_CUDA(cudaMemcpyAsync(Acp, sol, sizeof(T) * N, cudaMemcpyDeviceToDevice, s));
+        T* U = sc.alloc<T>((size_t)rows * kk);
+        T* S = sc.alloc<T>(kk);
+        T* Vt = sc.alloc<T>((size_t)kk * r1);
+        svd<T>(s, sc, rows, r1, Acp, rows, U, rows, S, Vt, kk);
+        // residual-norm truncation by bisection
+        const double thr = std::max(delta, 2.0 * res_sol);
+        int lo = 1, hi = kk;
+        T* cand = sc.alloc<T>(N);
+        T* SV = sc.alloc<T>((size_t)kk * r1);
+        scale_rows_kernel<T><<<grid_for((long long)kk * r1), 256, 0, s>>>(kk, r1, Vt, kk, S, SV, kk);
+        QTT_CHECK_LAUNCH();
+        while (lo < hi) {
+          int mid = (lo + hi) / 2;
+          gemm<T>(s, false, false, rows, r1, mid, T(1), U, rows, 0, SV, kk, 0, T(0), cand, rows, 0);
+          if (local_residual(k, XAX_L.p, r0, PhiR, r1, g, gn, cand) <= thr) hi = mid;
+          else lo = mid + 1;
+        }
+        int rk = hi;
+        if (max_rank > 0) rk = std::min(rk, std::max(1, max_rank - kick));
+        // truncated core xt = U_rk S V_rk^T
+        gemm<T>(s, false, false, rows, r1, rk, T(1), U, rows, 0, SV, kk, 0, T(0), cand, rows, 0);
+        // new residual-proxy core
+        const int rz0 = z->r[k], rz1 = z->r[k + 1];
+        T* zres = sc.alloc<T>((size_t)rz0 * n * rz1);
+        T* tmp = sc.alloc<T>((size_t)rz0 * n * rz1);
+        local_rhs(ZY_L.p, rz0, k, ZY_R[k + 1].p, rz1, zres, sc);
+        local_apply(ZAX_L.p, rz0, r0, k, ZAX_R[k + 1].p, rz1, r1, cand, tmp, sc);
+        axpby<T>(s, (size_t)rz0 * n * rz1, T(-1), tmp, T(1), zres);
+        const int zrows = rz0 * n, zk = std::min(zrows, rz1);
+        T* Qz = sc.alloc<T>((size_t)zrows * zk);
+        T* Rz = sc.alloc<T>((size_t)zk * rz1);
+        qr<T>(s, sc, zrows, rz1, zres, zrows, Qz, zrows, Rz, zk);
+        // enrichment block: residual on x's left and z's right interfaces
+        T* enr = sc.alloc<T>((size_t)r0 * n * rz1);
+        T* tmp2 = sc.alloc<T>((size_t)r0 * n * rz1);
+        local_rhs(XY_L.p, r0, k, ZY_R[k + 1].p, rz1, enr, sc);
+        local_apply(XAX_L.p, r0, r0, k, ZAX_R[k + 1].p, rz1, r1, cand, tmp2, sc);
+        axpby<T>(s, (size_t)r0 * n * rz1, T(-1), tmp2, T(1), enr);
+        // Uaug = [U_rk, enr]  ->  Q R
+        const int ca = rk + rz1, nk = std::min(rows, ca);
+        T* Uaug = sc.alloc<T>((size_t)rows * ca);
+        QTT_CUDA(cudaMemcpyAsync(Uaug, U, sizeof(T) * rows * rk, cudaMemcpyDeviceToDevice, s));
+        QTT_CUDA(cudaMemcpyAsync(Uaug + (size_t)rows * rk, enr, sizeof(T) * rows * rz1, cudaMemcpyDeviceToDevice, s));
+        T* Q = sc.alloc<T>((size_t)rows * nk);
+        T* Rq = sc.alloc<T>((size_t)nk * ca);
+        qr<T>(s, sc, rows, ca, Uaug, rows, Q, rows, Rq, nk);
+        // carry = R[:, :rk] (S V^T)[:rk, :]   (nk x r1)
+        T* carry = sc.alloc<T>((size_t)nk * r1);
+        gemm<T>(s, false, false, nk, r1, rk, T(1), Rq, nk, 0, SV, kk, 0, T(0), carry, nk, 0);
+        // next core <- carry * x_{k+1}
+        const int n2 = A->n[k + 1], r2 = x->r[k + 2];
+        T* nxt = sc.alloc<T>((size_t)nk * n2 * r2);
+        gemm<T>(s, false, false, nk, n2 * r2, r1, T(1), carry, nk, 0, (const T*)x->core[k + 1], r1, 0, T(0), nxt, nk,
+                0);
+        ensure_core(x, k, (size_t)rows * nk);
+        ensure_core(x, k + 1, (size_t)nk * n2 * r2);
+        QTT_CUDA(cudaMemcpyAsync(x->core[k], Q, sizeof(T) * rows * nk, cudaMemcpyDeviceToDevice, s));
+        QTT_CUDA(cudaMemcpyAsync(x->core[k + 1], nxt, sizeof(T) * nk * n2 * r2, cudaMemcpyDeviceToDevice, s));
+        x->r[k + 1] = nk;
+        // z core k <- Qz; next z core keeps its leading zk rows
+        const int zn2 = z->n[k + 1], zr2 = z->r[k + 2];
+        QTT_CUDA(cudaMemcpyAsync(z->core[k], Qz, sizeof(T) * zrows * zk, cudaMemcpyDeviceToDevice, s));
+        if (zk != rz1) {
+          T* znext = sc.alloc<T>((size_t)zk * zn2 * zr2);
+          copy2d<T>(s, zk, zn2 * zr2, (const T*)z->core[k + 1], rz1, znext, zk);
+          QTT_CUDA(cudaMemcpyAsync(z->core[k + 1], znext, sizeof(T) * zk * zn2 * zr2, cudaMemcpyDeviceToDevice, s));
+        }
+        z->r[k + 1] = zk;
+        // left interfaces
+        XAX_Ln.ensure((size_t)nk * rA(k + 1) * nk, s);
+        left_XAX(x, x, k, XAX_L.p, XAX_Ln.p, sc);
+        XY_Ln.ensure((size_t)nk * ry(k + 1), s);
+        left_XY(x, k, XY_L.p, XY_Ln.p, sc);
+        ZAX_Ln.ensure((size_t)zk * rA(k + 1) * nk, s);
+        left_XAX(z, x, k, ZAX_L.p, ZAX_Ln.p, sc);
+        ZY_Ln.ensure((size_t)zk * ry(k + 1), s);
+        left_XY(z, k, ZY_L.p, ZY_Ln.p, sc);
+        std::swap(XAX_L, XAX_Ln);
+        std::swap(XY_L, XY_Ln);
+        std::swap(ZAX_L, ZAX_Ln);
+        std::swap(ZY_L, ZY_Ln);
+      }
+      if (info) {
+        info->sweeps += 1;
+        info->max_local_res = max_res;
+      }
+      if (verbose) {
+        fprintf(stderr, "[qtt_solve %s] sweep %d max local res %.3e ranks", sizeof(T) == 8 ? "f64" : "f32", sweep + 1,
+                max_res);
+        for (int k = 0; k <= D; ++k) fprintf(stderr, " %d", x->r[k]);
+        fprintf(stderr, "\n");
+      }
+      if (max_res <= tol) {
+        status = QTT_OK;
+        break;
+      }
+    }
+    return status;
+  }
+};
+
+template <typename S, typename D>
+__global__ void cvt_kernel(const S* a, D* b, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) b[i] = (D)a[i];
+}
+
+Tptr default_x0(cudaStream_t s, const qtt_tensor* f, int prec) {
+  std::vector<int> r(f->d + 1, 1);
+  auto x = own(tensor_alloc(f->d, f->n, nullptr, r.data(), prec, 0));
+  for (int k = 0; k < f->d; ++k) {
+    if (prec == QTT_F64) fill<double>(s, (double*)x->core[k], f->n[k], 1.0);
+    else fill<float>(s, (float*)x->core[k], f->n[k], 1.0f);
+  }
+  return x;
+}
+
+Tptr default_z0(cudaStream_t s, const qtt_tensor* f, int rho, int prec) {
+  std::vector<int> r(f->d + 1, rho);
+  r[0] = r[f->d] = 1;
+  auto z = own(tensor_alloc(f->d, f->n, nullptr, r.data(), prec, 0));
+  for (int k = 0; k < f->d; ++k) {
+    long long e = (long long)core_elems(z.get(), k);
+    if (prec == QTT_F64) proxy_kernel<double><<<grid_for(e), 256, 0, s>>>((double*)z->core[k], e, k);
+    else proxy_kernel<float><<<grid_for(e), 256, 0, s>>>((float*)z->core[k], e, k);
+    QTT_CHECK_LAUNCH();
+  }
+  return z;
+}
+
+template <typename T>
+int amen_run(cudaStream_t s, const qtt_tensor* K, const qtt_tensor* f, qtt_tensor* x, qtt_tensor* z, double tol,
+             const qtt_solve_opts& o, qtt_solve_info* info) {
+  Arena ar(s);
+  Amen<T> am(s, ar);
+  am.A = K;
+  am.y = f;
+  am.x = x;
+  am.z = z;
+  am.D = K->d;
+  am.tol = tol;
+  am.max_rank = o.max_rank > 0 ? o.max_rank : 512;
+  am.kick = z->r[1];
+  am.max_sweeps = o.max_sweeps > 0 ? o.max_sweeps : 30;
+  am.ndir = o.local_direct_max > 0 ? o.local_direct_max : 2048;
+  am.restart = std::min(o.local_restart > 0 ? o.local_restart : 40, 64);
+  am.cycles = o.local_max_cycles > 0 ? o.local_max_cycles : 8;
+  am.verbose = o.verbose;
+  am.info = info;
+  am.dscal = ar.alloc<double>(4);
+  int rc = am.run();
+  QTT_CUDA(cudaStreamSynchronize(s));
+  return rc;
+}
+
+double erank_of(const qtt_tensor* x) {
+  const int d = x->d;
+  if (d == 1) return 1.0;
+  double S = 0;
+  for (int k = 0; k < d; ++k) S += (double)core_elems(x, k);
+  double a = 0, b = (double)x->n[0] * x->m[0] + (double)x->n[d - 1] * x->m[d - 1];
+  for (int k = 1; k < d - 1; ++k) a += (double)x->n[k] * x->m[k];
+  if (a == 0) return S / b;
+  return (-b + std::sqrt(b * b + 4 * a * S)) / (2 * a);
+}
+
+}  // namespace
+
+double residual64(cudaStream_t s, const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* f) {
+  Arena ar(s);
+  auto Ku = own(product<double>(s, K, u));
+  auto r = own(tt_sum<double>(s, 1.0, f, -1.0, Ku.get()));
+  double rn = norm<double>(s, ar, r.get());
+  double fn = norm<double>(s, ar, f);
+  return fn > 0 ? rn / fn : rn;
+}
+
+int solve(const qtt_tensor* K, const qtt_tensor* f, const qtt_tensor* x0, const qtt_tensor* z0,
+          const qtt_solve_opts* opts, qtt_tensor** xout, qtt_solve_info* info, cudaStream_t s) {
+  QTT_REQUIRE(K && f && opts && xout, "qtt_solve: null argument");
+  QTT_REQUIRE(K->is_matrix && !f->is_matrix && K->d == f->d, "qtt_solve: K must be an MPO and f an MPS of equal length");
+  for (int k = 0; k < K->d; ++k)
+    QTT_REQUIRE(K->n[k] == f->n[k] && K->m[k] == f->n[k], "qtt_solve: mode sizes of K and f differ");
+  QTT_REQUIRE(opts->tol > 0, "qtt_solve: tol must be positive");
+  qtt_solve_opts o = *opts;
+  qtt_solve_info local{};
+  qtt_solve_info* inf = info ? info : &local;
+  std::memset(inf, 0, sizeof(*inf));
+  const int rho = o.kick_rank > 0 ? o.kick_rank : 4;
+  int rc = QTT_OK;
+  if (o.precision == QTT_F64 || o.precision == QTT_F32) {
+    const int prec = o.precision;
+    QTT_REQUIRE(prec == QTT_F32 || (K->prec == QTT_F64 && f->prec == QTT_F64), "qtt_solve: FP64 solve needs FP64 K, f");
+    Tptr Kc = own(nullptr), fc = own(nullptr);
+    const qtt_tensor* Ku = K;
+    const qtt_tensor* fu = f;
+    if (K->prec != prec) { Kc = own(tensor_clone(K, prec, s)); Ku = Kc.get(); }
+    if (f->prec != prec) { fc = own(tensor_clone(f, prec, s)); fu = fc.get(); }
+    Tptr x = x0 ? own(tensor_clone(x0, prec, s)) : default_x0(s, f, prec);
+    Tptr z = z0 ? own(tensor_clone(z0, prec, s)) : default_z0(s, f, rho, prec);
+    rc = prec == QTT_F64 ? amen_run<double>(s, Ku, fu, x.get(), z.get(), o.tol, o, inf)
+                         : amen_run<float>(s, Ku, fu, x.get(), z.get(), o.tol, o, inf);
+    if (prec == QTT_F64) {
+      inf->rel_residual = residual64(s, K, x.get(), f);
+    }
+    *xout = x.release();
+  } else {
+    QTT_REQUIRE(o.precision == QTT_MIXED, "qtt_solve: unknown precision");
+    QTT_REQUIRE(K->prec == QTT_F64 && f->prec == QTT_F64, "qtt_solve: mixed precision needs FP64 K and f");
+    const double inner = o.inner_tol > 0 ? o.inner_tol : 1e-5;
+    const int refine_max = o.refine_max > 0 ? o.refine_max : 6;
+    auto K32 = own(tensor_clone(K, QTT_F32, s));
+    Tptr u = x0 ? own(tensor_clone(x0, QTT_F64, s)) : own(nullptr);
+    Tptr z = z0 ? own(tensor_clone(z0, QTT_F32, s)) : default_z0(s, f, rho, QTT_F32);
+    const double fn = [&] {
+      Arena ar(s);
+      return norm<double>(s, ar, f);
+    }();
+    rc = QTT_ENOCONV;
+    for (int it = 0; it <= refine_max; ++it) {
+      // r = f - K u  (FP64 matvec, FP64 rounding)
+      Tptr r = own(nullptr);
+      double rel = 1.0;
+      {
+        Arena ar(s);
+        if (u) {
+          auto Ku = own(product<double>(s, K, u.get()));
+          r = own(tt_sum<double>(s, 1.0, f, -1.0, Ku.get()));
+        } else {
+          r = own(tensor_clone(f, QTT_F64, s));
+        }
+        left_orthogonalize<double>(s, ar, r.get(), r->d - 1);
+        double* dv = ar.alloc<double>(1);
+        sumsq<double>(s, (const double*)r->core[r->d - 1], core_elems(r.get(), r->d - 1), dv);
+        double rn2 = 0;
+        QTT_CUDA(cudaMemcpyAsync(&rn2, dv, sizeof(double), cudaMemcpyDeviceToHost, s));
+        QTT_CUDA(cudaStreamSynchronize(s));
+        rel = std::sqrt(rn2) / (fn > 0 ? fn : 1.0);
+        inf->rel_residual = rel;
+        if (o.verbose) fprintf(stderr, "[qtt_solve mixed] refinement %d: rel residual %.3e\n", it, rel);
+        if (rel <= o.tol || it == refine_max) {
+          rc = rel <= o.tol ? QTT_OK : QTT_ENOCONV;
+          break;
+        }
+        round_tt<double>(s, ar, r.get(), std::min(1e-2, 0.1 * inner), 0);
+      }
+      auto r32 = own(tensor_clone(r.get(), QTT_F32, s));
+      auto d32 = default_x0(s, f, QTT_F32);
+      amen_run<float>(s, K32.get(), r32.get(), d32.get(), z.get(), inner, o, inf);
+      auto d64 = own(tensor_clone(d32.get(), QTT_F64, s));
+      if (!u) {
+        u = std::move(d64);
+      } else {
+        u = own(tt_sum<double>(s, 1.0, u.get(), 1.0, d64.get()));
+      }
+      Arena ar(s);
+      round_tt<double>(s, ar, u.get(), std::max(1e-15, 1e-3 * o.tol), o.max_rank > 0 ? o.max_rank : 0);
+      inf->refinements += 1;
+    }
+    if (!u) u = default_x0(s, f, QTT_F64);
+    *xout = u.release();
+  }
+  inf->status = rc;
+  int mr = 0;
+  for (int k = 0; k <= (*xout)->d; ++k) mr = std::max(mr, (*xout)->r[k]);
+  inf->max_rank = mr;
+  inf->erank = erank_of(*xout);
+  return rc;
+}
+
+}  // namespace qtt
+
+extern "C" int qtt_solve(const qtt_tensor* K, const qtt_tensor* f, const qtt_tensor* x0, const qtt_tensor* z0,
+                         const qtt_solve_opts* opts, qtt_tensor** x, qtt_solve_info* info, void* stream) {
+  try {
+    int rc = qtt::solve(K, f, x0, z0, opts, x, info, reinterpret_cast<cudaStream_t>(stream));
+    if (rc == QTT_ENOCONV) qtt::set_last_error("qtt_solve: tolerance not reached");
+    return rc;
+  } catch (const qtt::QttError& e) {
+    qtt::set_last_error(e.what());
+    if (info) info->status = e.code;
+    return e.code;
+  } catch (const std::exception& e) {
+    qtt::set_last_error(e.what());
+    return QTT_EINVAL;
+  }
+}

@@ -1,0 +1,169 @@
+// Shared internals of the QTT engine: error handling, device scratch arena,
+// the tensor object, and declarations of the dense kernels every stage uses.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/qtt.h"
+
+namespace qtt {
+
+// ---------------------------------------------------------------------------
+// Errors: internal code throws QttError; the C ABI catches and returns codes.
+// ---------------------------------------------------------------------------
+struct QttError : public std::runtime_error {
+  int code;
+  QttError(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+void set_last_error(const std::string& msg);
+
+#define QTT_CUDA(call)                                                              \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      throw ::qtt::QttError(e_ == cudaErrorMemoryAllocation ? QTT_ENOMEM : QTT_ECUDA, \
+                            std::string(#call) + ": " + cudaGetErrorString(e_) +      \
+                                " (" __FILE__ ":" + std::to_string(__LINE__) + ")"); \
+    }                                                                               \
+  } while (0)
+
+#define QTT_CHECK_LAUNCH() QTT_CUDA(cudaGetLastError())
+
+#define QTT_REQUIRE(cond, msg)                                             \
+  do {                                                                     \
+    if (!(cond)) throw ::qtt::QttError(QTT_EINVAL, std::string(msg));      \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// Scratch arena: stream-ordered allocations released together.
+// ---------------------------------------------------------------------------
+class Arena {
+ public:
+  explicit Arena(cudaStream_t s) : stream_(s) {}
+  ~Arena() { release(); }
+  Arena(const Arena&) = delete;
+  Arena& operator=(const Arena&) = delete;
+  void* raw(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, bytes, stream_);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw QttError(QTT_ENOMEM, "scratch allocation of " + std::to_string(bytes) + " bytes failed");
+    }
+    ptrs_.push_back(p);
+    return p;
+  }
+  template <typename T>
+  T* alloc(size_t n) { return static_cast<T*>(raw(n * sizeof(T))); }
+  void release() {
+    for (void* p : ptrs_) cudaFreeAsync(p, stream_);
+    ptrs_.clear();
+  }
+  cudaStream_t stream() const { return stream_; }
+
+ private:
+  cudaStream_t stream_;
+  std::vector<void*> ptrs_;
+};
+
+}  // namespace qtt
+
+// ---------------------------------------------------------------------------
+// Tensor object (opaque to C callers).
+// ---------------------------------------------------------------------------
+struct qtt_tensor {
+  int d = 0;
+  int is_matrix = 0;
+  int prec = QTT_F64;
+  int n[QTT_MAX_CORES] = {0};
+  int m[QTT_MAX_CORES] = {0};
+  int r[QTT_MAX_CORES + 1] = {0};
+  void* core[QTT_MAX_CORES] = {nullptr};
+  size_t cap[QTT_MAX_CORES] = {0};   // elements allocated per core
+};
+
+namespace qtt {
+
+inline size_t esize(int prec) { return prec == QTT_F32 ? 4 : 8; }
+inline size_t core_elems(const qtt_tensor* t, int k) {
+  return (size_t)t->r[k] * t->n[k] * t->m[k] * t->r[k + 1];
+}
+
+qtt_tensor* tensor_alloc(int d, const int* n, const int* m, const int* r, int prec, int is_matrix);
+void tensor_free(qtt_tensor* t);
+// Make sure core k can hold `elems` elements (reallocates, discarding content).
+void tensor_reserve(qtt_tensor* t, int k, size_t elems, cudaStream_t s);
+qtt_tensor* tensor_clone(const qtt_tensor* src, int prec, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Dense kernels (column-major).  All are asynchronous on `s`.
+// ---------------------------------------------------------------------------
+// C = alpha op(A) op(B) + beta C, strided batch.
+template <typename T>
+void gemm(cudaStream_t s, bool tA, bool tB, int M, int N, int K, T alpha, const T* A, int lda,
+          long long sA, const T* B, int ldb, long long sB, T beta, T* C, int ldc, long long sC,
+          int batch = 1);
+
+// out = permutation of a column-major tensor: out dim k is input dim perm[k].
+template <typename T>
+void permute(cudaStream_t s, const T* in, T* out, int nd, const int* dims, const int* perm, T alpha = T(1),
+             T beta = T(0));
+
+template <typename T>
+void fill(cudaStream_t s, T* p, size_t n, T v);
+
+// y = a x + b y
+template <typename T>
+void axpby(cudaStream_t s, size_t n, T a, const T* x, T b, T* y);
+
+// strided 2D copy: dst[i + j ldd] = src[i + j lds], i < rows, j < cols
+template <typename T>
+void copy2d(cudaStream_t s, int rows, int cols, const T* src, int lds, T* dst, int ldd);
+
+// convert precision
+template <typename S, typename D>
+void convert(cudaStream_t s, const S* src, D* dst, size_t n);
+
+// out[0] = sum x^2 (device scalar, accumulated in double)
+template <typename T>
+void sumsq(cudaStream_t s, const T* x, size_t n, double* out);
+// out[0] = sum x*y (device, double accumulation)
+template <typename T>
+void dotp(cudaStream_t s, const T* x, const T* y, size_t n, double* out);
+
+// Einstein-summation contraction of two dense column-major operands
+// (first index fastest), e.g. "aib,bBd->aiBd".  Labels are single chars;
+// an index in both inputs but not in the output is summed; an index in both
+// inputs and the output is a batch index.  C = alpha A*B + beta C.
+template <typename T>
+void einsum(cudaStream_t s, Arena& ar, const char* spec, const T* A, const int* dA, const T* B, const int* dB,
+            T* C, T alpha = T(1), T beta = T(0));
+
+// ---------------------------------------------------------------------------
+// Dense factorizations (column-major).
+// ---------------------------------------------------------------------------
+// Householder QR of the m x n matrix A (lda): on return Q (m x k, ldq) and R
+// (k x n, ldr) with k = min(m, n).  A is destroyed.
+template <typename T>
+void qr(cudaStream_t s, Arena& ar, int m, int n, T* A, int lda, T* Q, int ldq, T* R, int ldr);
+
+// Thin SVD of the m x n matrix A: U (m x k), S (k), Vt (k x n), k = min(m,n),
+// singular values descending.  A is destroyed.
+template <typename T>
+void svd(cudaStream_t s, Arena& ar, int m, int n, T* A, int lda, T* U, int ldu, T* S, T* Vt, int ldvt);
+
+// Solve A X = B (A n x n, B n x nrhs) by LU with partial pivoting.  A and B
+// are overwritten (B holds X).  Returns nonzero info on device in *info if a
+// pivot is exactly zero.
+template <typename T>
+void lu_solve(cudaStream_t s, Arena& ar, int n, T* A, int lda, T* B, int ldb, int nrhs, int* info);
+
+}  // namespace qtt

@@ -1,0 +1,487 @@
+// Dense factorizations written from the textbook mathematics:
+//  * Householder QR in compact WY form (Golub & Van Loan, Sec. 5.1-5.2):
+//    single-CTA panel factorisation of 32 columns, trailing update and the
+//    explicit Q by three GEMMs per panel;
+//  * one-sided (Hestenes) Jacobi SVD of the triangular factor with the
+//    round-robin parallel ordering (Demmel & Veselic 1992);
+//  * LU with partial pivoting: single-CTA panel, triangular solve of the
+//    block row and GEMM trailing update; blocked triangular solves.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace qtt {
+namespace {
+
+constexpr int NB = 32;         // panel width
+constexpr int PT = 1024;       // panel kernel threads
+
+__device__ __forceinline__ double wsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
+__device__ double block_sum(double v, double* red) {
+  v = wsum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = l < (int)(blockDim.x >> 5) ? red[l] : 0.0;
+    r = wsum(r);
+    if (l == 0) red[32] = r;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// Householder panel: A is the m x jb panel (lda), V receives the reflectors
+// (m x jb, ld ldv, unit diagonal, zeros above), Tm the jb x jb upper
+// triangular factor (ld NB) with H_1..H_jb = I - V Tm V^T.
+template <typename T>
+__global__ void __launch_bounds__(PT) qr_panel_kernel(int m, int jb, T* A, int lda, T* V, int ldv, T* Tm) {
+  __shared__ double red[33];
+  __shared__ double s_tau, s_scale, s_beta;
+  __shared__ double y[NB];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int c = 0; c < jb; ++c) {
+    T* a = A + (long long)c * lda;
+    double part = 0.0;
+    for (int i = c + 1 + tid; i < m; i += PT) part += (double)a[i] * (double)a[i];
+    double sigma = block_sum<T>(part, red);
+    if (tid == 0) {
+      double alpha = (c < m) ? (double)a[c] : 0.0;
+      double tau = 0.0, scale = 0.0, beta = alpha;
+      if (sigma > 0.0) {
+        double nrm = sqrt(alpha * alpha + sigma);
+        beta = alpha >= 0.0 ? -nrm : nrm;
+        tau = (beta - alpha) / beta;
+        scale = 1.0 / (alpha - beta);
+      }
+      s_tau = tau;
+      s_scale = scale;
+      s_beta = beta;
+    }
+    __syncthreads();
+    const double tau = s_tau, scale = s_scale;
+    T* v = V + (long long)c * ldv;
+    for (int i = tid; i < m; i += PT) {
+      if (i < c) v[i] = T(0);
+      else if (i == c) v[i] = T(1);
+      else {
+        T vi = (T)((double)a[i] * scale);
+        v[i] = vi;
+        a[i] = vi;
+      }
+    }
+    if (tid == 0 && c < m) a[c] = (T)s_beta;
+    __syncthreads();
+    // apply H_c to the remaining panel columns (one warp per column)
+    for (int j = c + 1 + warp; j < jb; j += PT / 32) {
+      T* aj = A + (long long)j * lda;
+      double d = 0.0;
+      for (int i = c + lane; i < m; i += 32) d += (double)v[i] * (double)aj[i];
+      d = wsum(d) * tau;
+      for (int i = c + lane; i < m; i += 32) aj[i] = (T)((double)aj[i] - d * (double)v[i]);
+    }
+    // T column: T[0:c, c] = -tau T[0:c, 0:c] (V[:, 0:c]^T v_c), T[c, c] = tau
+    for (int w = warp; w < c; w += PT / 32) {
+      const T* vw = V + (long long)w * ldv;
+      double d = 0.0;
+      for (int i = c + lane; i < m; i += 32) d += (double)vw[i] * (double)v[i];
+      d = wsum(d);
+      if (lane == 0) y[w] = d;
+    }
+    __syncthreads();
+    if (tid < c) {
+      double acc = 0.0;
+      for (int s2 = tid; s2 < c; ++s2) acc += (double)Tm[tid + s2 * NB] * y[s2];
+      Tm[tid + c * NB] = (T)(-tau * acc);
+    }
+    if (tid == 0) Tm[c + c * NB] = (T)tau;
+    for (int t = tid; t < NB; t += PT)
+      if (t > c) Tm[t + c * NB] = T(0);
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void set_identity_kernel(T* Q, int m, int k, int ldq) {
+  long long total = (long long)m * k;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(t % m), j = (int)(t / m);
+    Q[i + (long long)j * ldq] = (i == j) ? T(1) : T(0);
+  }
+}
+
+template <typename T>
+__global__ void upper_copy_kernel(const T* A, int lda, T* R, int ldr, int k, int n) {
+  long long total = (long long)k * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(t % k), j = (int)(t / k);
+    R[i + (long long)j * ldr] = (i <= j) ? A[i + (long long)j * lda] : T(0);
+  }
+}
+
+inline int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 2432)); }
+
+// ---------------------------------------------------------------------------
+// One-sided Jacobi on W (m x n, ldw) accumulating V (n x n, ldv); single CTA.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(1024) jacobi_kernel(int m, int n, T* W, int ldw, T* Vm, int ldv, int max_sweeps,
+                                                      int* sweeps_out) {
+  __shared__ int rotated;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int np = n + (n & 1);                  // even number of positions
+  const double tol = 1e-15 * (double)(m > 1 ? m : 1);
+  const double tolf = (sizeof(T) == 4) ? 1e-7 * (double)(m > 1 ? m : 1) : tol;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int round = 0; round < np - 1; ++round) {
+      for (int pi = warp; pi < np / 2; pi += nw) {
+        // pair number pi of round `round` in the round-robin tournament
+        int p, q;
+        if (pi == 0) {
+          p = round % (np - 1);
+          q = np - 1;
+        } else {
+          p = (round + pi) % (np - 1);
+          q = (round - pi + (np - 1)) % (np - 1);
+        }
+        if (p > q) { int t = p; p = q; q = t; }
+        if (q >= n) continue;                  // dummy position for odd n
+        T* wp = W + (long long)p * ldw;
+        T* wq = W + (long long)q * ldw;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int i = lane; i < m; i += 32) {
+          double a = wp[i], b = wq[i];
+          al += a * a;
+          be += b * b;
+          ga += a * b;
+        }
+        al = wsum(al);
+        be = wsum(be);
+        ga = wsum(ga);
+        if (ga == 0.0 || !(fabs(ga) > tolf * sqrt(al * be))) continue;
+        double zeta = (be - al) / (2.0 * ga);
+        double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+        for (int i = lane; i < m; i += 32) {
+          double a = wp[i], b = wq[i];
+          wp[i] = (T)(cs * a - sn * b);
+          wq[i] = (T)(sn * a + cs * b);
+        }
+        T* vp = Vm + (long long)p * ldv;
+        T* vq = Vm + (long long)q * ldv;
+        for (int i = lane; i < n; i += 32) {
+          double a = vp[i], b = vq[i];
+          vp[i] = (T)(cs * a - sn * b);
+          vq[i] = (T)(sn * a + cs * b);
+        }
+        if (lane == 0) rotated = 1;
+      }
+      __syncthreads();
+    }
+    if (!rotated) break;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && sweeps_out) *sweeps_out = sweep;
+}
+
+// column norms -> S, normalise W columns, then sort descending (order[])
+template <typename T>
+__global__ void __launch_bounds__(1024) svd_finish_kernel(int m, int n, T* W, int ldw, T* S, int* order) {
+  extern __shared__ double sh[];
+  double* sv = sh;                       // n values
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = warp; j < n; j += nw) {
+    T* w = W + (long long)j * ldw;
+    double s = 0.0;
+    for (int i = lane; i < m; i += 32) s += (double)w[i] * (double)w[i];
+    s = sqrt(wsum(s));
+    if (lane == 0) sv[j] = s;
+    if (s > 0.0)
+      for (int i = lane; i < m; i += 32) w[i] = (T)((double)w[i] / s);
+  }
+  __syncthreads();
+  // rank of each value (descending, ties by index) -> position
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    int rank = 0;
+    double v = sv[j];
+    for (int t = 0; t < n; ++t) {
+      double u = sv[t];
+      if (u > v || (u == v && t < j)) ++rank;
+    }
+    order[rank] = j;
+    S[rank] = (T)v;
+  }
+}
+
+template <typename T>
+__global__ void gather_cols_kernel(const T* src, int lds, T* dst, int ldd, int rows, int ncols, const int* order,
+                                   bool transpose_out) {
+  long long total = (long long)rows * ncols;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(t % rows), j = (int)(t / rows);
+    T v = src[i + (long long)order[j] * lds];
+    if (transpose_out) dst[j + (long long)i * ldd] = v;
+    else dst[i + (long long)j * ldd] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// LU panel with partial pivoting: factor columns [j0, j0 + jb) of the full
+// n x n matrix A, swapping whole rows of A and of B (nrhs columns).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(PT) lu_panel_kernel(int n, int j0, int jb, T* A, int lda, T* B, int ldb, int nrhs,
+                                                      int* info) {
+  __shared__ double rv[32];
+  __shared__ int ri[32];
+  __shared__ int s_piv;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int c = j0; c < j0 + jb; ++c) {
+    T* col = A + (long long)c * lda;
+    double best = -1.0;
+    int bi = c;
+    for (int i = c + tid; i < n; i += PT) {
+      double v = fabs((double)col[i]);
+      if (v > best) { best = v; bi = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) { rv[warp] = best; ri[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double b = -1.0;
+      int p = c;
+      for (int w = 0; w < PT / 32; ++w)
+        if (rv[w] > b || (rv[w] == b && ri[w] < p)) { b = rv[w]; p = ri[w]; }
+      s_piv = p;
+      if (b == 0.0 && info) atomicExch(info, c + 1);
+    }
+    __syncthreads();
+    const int p = s_piv;
+    if (p != c) {
+      for (int j = tid; j < n; j += PT) {
+        T t = A[c + (long long)j * lda];
+        A[c + (long long)j * lda] = A[p + (long long)j * lda];
+        A[p + (long long)j * lda] = t;
+      }
+      for (int j = tid; j < nrhs; j += PT) {
+        T t = B[c + (long long)j * ldb];
+        B[c + (long long)j * ldb] = B[p + (long long)j * ldb];
+        B[p + (long long)j * ldb] = t;
+      }
+    }
+    __syncthreads();
+    const double piv = (double)col[c];
+    const double inv = piv != 0.0 ? 1.0 / piv : 0.0;
+    for (int i = c + 1 + tid; i < n; i += PT) col[i] = (T)((double)col[i] * inv);
+    __syncthreads();
+    // rank-1 update of the rest of the panel (one warp per column)
+    for (int j = c + 1 + warp; j < j0 + jb; j += PT / 32) {
+      T* aj = A + (long long)j * lda;
+      const double u = (double)aj[c];
+      for (int i = c + 1 + lane; i < n; i += 32) aj[i] = (T)((double)aj[i] - (double)col[i] * u);
+    }
+    __syncthreads();
+  }
+}
+
+// U12 = L11^{-1} A12 for a unit lower jb x jb block: one thread per column
+template <typename T>
+__global__ void trsm_lower_unit_kernel(int jb, const T* L, int ldl, T* X, int ldx, int ncols) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ncols) return;
+  T* x = X + (long long)j * ldx;
+  for (int i = 0; i < jb; ++i) {
+    double v = (double)x[i];
+    for (int k = 0; k < i; ++k) v -= (double)L[i + (long long)k * ldl] * (double)x[k];
+    x[i] = (T)v;
+  }
+}
+
+// solve a small triangular block in place (one thread per rhs column)
+template <typename T>
+__global__ void trsv_block_kernel(int nb, const T* A, int lda, T* X, int ldx, int ncols, bool upper) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ncols) return;
+  T* x = X + (long long)j * ldx;
+  if (!upper) {
+    for (int i = 0; i < nb; ++i) {
+      double v = (double)x[i];
+      for (int k = 0; k < i; ++k) v -= (double)A[i + (long long)k * lda] * (double)x[k];
+      x[i] = (T)v;
+    }
+  } else {
+    for (int i = nb - 1; i >= 0; --i) {
+      double v = (double)x[i];
+      for (int k = i + 1; k < nb; ++k) v -= (double)A[i + (long long)k * lda] * (double)x[k];
+      double d = (double)A[i + (long long)i * lda];
+      x[i] = (T)(d != 0.0 ? v / d : 0.0);
+    }
+  }
+}
+
+}  // namespace
+
+template <typename T>
+void qr(cudaStream_t s, Arena& ar, int m, int n, T* A, int lda, T* Q, int ldq, T* R, int ldr) {
+  QTT_REQUIRE(m >= 1 && n >= 1, "qr: empty matrix");
+  const int k = std::min(m, n);
+  T* Vall = ar.alloc<T>((size_t)m * k);
+  const int nblk = (k + NB - 1) / NB;
+  T* Tall = ar.alloc<T>((size_t)NB * NB * nblk);
+  T* W1 = ar.alloc<T>((size_t)NB * std::max(n, k));
+  T* W2 = ar.alloc<T>((size_t)NB * std::max(n, k));
+  for (int b = 0; b < nblk; ++b) {
+    const int j0 = b * NB, jb = std::min(NB, k - j0), mm = m - j0;
+    T* Vb = Vall + j0 + (long long)j0 * m;
+    T* Tb = Tall + (long long)b * NB * NB;
+    // zero the rows above j0 of this block's V columns
+    if (j0 > 0) {
+      for (int c = 0; c < jb; ++c) QTT_CUDA(cudaMemsetAsync(Vall + (long long)(j0 + c) * m, 0, sizeof(T) * j0, s));
+    }
+    qr_panel_kernel<T><<<1, PT, 0, s>>>(mm, jb, A + j0 + (long long)j0 * lda, lda, Vb, m, Tb);
+    QTT_CHECK_LAUNCH();
+    const int n2 = n - j0 - jb;
+    if (n2 > 0) {
+      T* C = A + j0 + (long long)(j0 + jb) * lda;
+      gemm<T>(s, true, false, jb, n2, mm, T(1), Vb, m, 0, C, lda, 0, T(0), W1, jb, 0);
+      gemm<T>(s, true, false, jb, n2, jb, T(1), Tb, NB, 0, W1, jb, 0, T(0), W2, jb, 0);
+      gemm<T>(s, false, false, mm, n2, jb, T(-1), Vb, m, 0, W2, jb, 0, T(1), C, lda, 0);
+    }
+  }
+  if (R) {
+    upper_copy_kernel<T><<<grid_for((long long)k * n), 256, 0, s>>>(A, lda, R, ldr, k, n);
+    QTT_CHECK_LAUNCH();
+  }
+  if (Q) {
+    set_identity_kernel<T><<<grid_for((long long)m * k), 256, 0, s>>>(Q, m, k, ldq);
+    QTT_CHECK_LAUNCH();
+    for (int b = nblk - 1; b >= 0; --b) {
+      const int j0 = b * NB, jb = std::min(NB, k - j0), mm = m - j0, nc = k - j0;
+      T* Vb = Vall + j0 + (long long)j0 * m;
+      T* Tb = Tall + (long long)b * NB * NB;
+      T* Qs = Q + j0 + (long long)j0 * ldq;
+      gemm<T>(s, true, false, jb, nc, mm, T(1), Vb, m, 0, Qs, ldq, 0, T(0), W1, jb, 0);
+      gemm<T>(s, false, false, jb, nc, jb, T(1), Tb, NB, 0, W1, jb, 0, T(0), W2, jb, 0);
+      gemm<T>(s, false, false, mm, nc, jb, T(-1), Vb, m, 0, W2, jb, 0, T(1), Qs, ldq, 0);
+    }
+  }
+}
+
+template <typename T>
+void svd(cudaStream_t s, Arena& ar, int m, int n, T* A, int lda, T* U, int ldu, T* S, T* Vt, int ldvt) {
+  QTT_REQUIRE(m >= 1 && n >= 1, "svd: empty matrix");
+  if (m < n) {
+    // SVD of A^T: A^T = U' S V'^T  =>  A = V' S U'^T
+    T* At = ar.alloc<T>((size_t)n * m);
+    int dims[2] = {m, n}, perm[2] = {1, 0};
+    if (lda == m) {
+      permute<T>(s, A, At, 2, dims, perm);
+    } else {
+      T* Ac = ar.alloc<T>((size_t)m * n);
+      copy2d<T>(s, m, n, A, lda, Ac, m);
+      permute<T>(s, Ac, At, 2, dims, perm);
+    }
+    const int k = m;
+    T* Ut = ar.alloc<T>((size_t)n * k);
+    T* Vtt = ar.alloc<T>((size_t)k * m);
+    svd<T>(s, ar, n, m, At, n, Ut, n, S, Vtt, k);
+    // U = V'  (m x k) = Vtt^T ; Vt = U'^T (k x n)
+    int d1[2] = {k, m}, d2[2] = {n, k};
+    T* tmp1 = ar.alloc<T>((size_t)m * k);
+    permute<T>(s, Vtt, tmp1, 2, d1, perm);
+    copy2d<T>(s, m, k, tmp1, m, U, ldu);
+    T* tmp2 = ar.alloc<T>((size_t)k * n);
+    permute<T>(s, Ut, tmp2, 2, d2, perm);
+    copy2d<T>(s, k, n, tmp2, k, Vt, ldvt);
+    return;
+  }
+  const int k = n;
+  T* Q = ar.alloc<T>((size_t)m * k);
+  T* R = ar.alloc<T>((size_t)k * n);
+  qr<T>(s, ar, m, n, A, lda, Q, m, R, k);
+  T* Vm = ar.alloc<T>((size_t)n * n);
+  set_identity_kernel<T><<<grid_for((long long)n * n), 256, 0, s>>>(Vm, n, n, n);
+  QTT_CHECK_LAUNCH();
+  jacobi_kernel<T><<<1, 1024, 0, s>>>(k, n, R, k, Vm, n, 40, nullptr);
+  QTT_CHECK_LAUNCH();
+  int* order = ar.alloc<int>(n);
+  svd_finish_kernel<T><<<1, 1024, sizeof(double) * n, s>>>(k, n, R, k, S, order);
+  QTT_CHECK_LAUNCH();
+  // U_R columns reordered, U = Q U_R
+  T* UR = ar.alloc<T>((size_t)k * k);
+  gather_cols_kernel<T><<<grid_for((long long)k * k), 256, 0, s>>>(R, k, UR, k, k, k, order, false);
+  QTT_CHECK_LAUNCH();
+  gemm<T>(s, false, false, m, k, k, T(1), Q, m, 0, UR, k, 0, T(0), U, ldu, 0);
+  // Vt = V^T with columns reordered
+  gather_cols_kernel<T><<<grid_for((long long)n * k), 256, 0, s>>>(Vm, n, Vt, ldvt, n, k, order, true);
+  QTT_CHECK_LAUNCH();
+}
+
+template <typename T>
+void lu_solve(cudaStream_t s, Arena& ar, int n, T* A, int lda, T* B, int ldb, int nrhs, int* info) {
+  QTT_REQUIRE(n >= 1, "lu_solve: empty system");
+  if (info) QTT_CUDA(cudaMemsetAsync(info, 0, sizeof(int), s));
+  for (int j0 = 0; j0 < n; j0 += NB) {
+    const int jb = std::min(NB, n - j0);
+    lu_panel_kernel<T><<<1, PT, 0, s>>>(n, j0, jb, A, lda, B, ldb, nrhs, info);
+    QTT_CHECK_LAUNCH();
+    const int n2 = n - j0 - jb;
+    if (n2 > 0) {
+      T* L11 = A + j0 + (long long)j0 * lda;
+      T* A12 = A + j0 + (long long)(j0 + jb) * lda;
+      trsm_lower_unit_kernel<T><<<(n2 + 127) / 128, 128, 0, s>>>(jb, L11, lda, A12, lda, n2);
+      QTT_CHECK_LAUNCH();
+      T* L21 = A + (j0 + jb) + (long long)j0 * lda;
+      T* A22 = A + (j0 + jb) + (long long)(j0 + jb) * lda;
+      gemm<T>(s, false, false, n2, n2, jb, T(-1), L21, lda, 0, A12, lda, 0, T(1), A22, lda, 0);
+    }
+  }
+  // forward: L y = B (unit lower), blocked
+  for (int j0 = 0; j0 < n; j0 += NB) {
+    const int jb = std::min(NB, n - j0);
+    trsv_block_kernel<T><<<(nrhs + 63) / 64, 64, 0, s>>>(jb, A + j0 + (long long)j0 * lda, lda, B + j0, ldb, nrhs,
+                                                         false);
+    QTT_CHECK_LAUNCH();
+    const int n2 = n - j0 - jb;
+    if (n2 > 0)
+      gemm<T>(s, false, false, n2, nrhs, jb, T(-1), A + (j0 + jb) + (long long)j0 * lda, lda, 0, B + j0, ldb, 0,
+              T(1), B + j0 + jb, ldb, 0);
+  }
+  // backward: U x = y
+  const int nblk = (n + NB - 1) / NB;
+  for (int b = nblk - 1; b >= 0; --b) {
+    const int j0 = b * NB, jb = std::min(NB, n - j0);
+    trsv_block_kernel<T><<<(nrhs + 63) / 64, 64, 0, s>>>(jb, A + j0 + (long long)j0 * lda, lda, B + j0, ldb, nrhs,
+                                                         true);
+    QTT_CHECK_LAUNCH();
+    if (j0 > 0)
+      gemm<T>(s, false, false, j0, nrhs, jb, T(-1), A + (long long)j0 * lda, lda, 0, B + j0, ldb, 0, T(1), B, ldb,
+              0);
+  }
+}
+
+template void qr<double>(cudaStream_t, Arena&, int, int, double*, int, double*, int, double*, int);
+template void qr<float>(cudaStream_t, Arena&, int, int, float*, int, float*, int, float*, int);
+template void svd<double>(cudaStream_t, Arena&, int, int, double*, int, double*, int, double*, double*, int);
+template void svd<float>(cudaStream_t, Arena&, int, int, float*, int, float*, int, float*, float*, int);
+template void lu_solve<double>(cudaStream_t, Arena&, int, double*, int, double*, int, int, int*);
+template void lu_solve<float>(cudaStream_t, Arena&, int, float*, int, float*, int, int, int*);
+
+}  // namespace qtt

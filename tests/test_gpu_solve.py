@@ -1,0 +1,75 @@
+"""GPU AMEn solve (qtt_solve) against the oracle: the full displacement
+vector against the sparse direct FE solution (relative L2 <= 1e-8 in FP64 at
+tolerance 1e-10), the oracle's own AMEn on the same inputs, the multi-patch
+concatenated system, and mixed precision with FP64 refinement."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import amen, assembly, fem, tt
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2501_07778_gb300 as q  # noqa: E402
+
+
+def _x0z0(prob, rx=2, rz=4, seed=5):
+    modes = W.qtt_modes(prob)
+    x0 = W.random_tt(seed, modes, [1] + [rx] * (len(modes) - 1) + [1])
+    z0 = W.random_tt(seed + 1, modes, [1] + [rz] * (len(modes) - 1) + [1])
+    return x0, z0
+
+
+@pytest.mark.parametrize("make,L", [(W.plate_body_force, 3), (W.plate_body_force, 5), (W.lshape_shear, 3)])
+def test_solve_matches_sparse_direct(make, L):
+    prob = make(L)
+    K, f = q.qtt_assemble_stiffness(prob)
+    x0, z0 = _x0z0(prob)
+    u, info = q.qtt_solve(K, f, q.QTT.from_cores(x0), q.QTT.from_cores(z0), tol=1e-10, max_sweeps=40)
+    assert info["rc"] == 0, info
+    ug = q.qtt_to_full(u).cpu().numpy()
+    ref = fem.solve_duplicated(prob)
+    err = np.linalg.norm(ug - ref) / np.linalg.norm(ref)
+    assert err <= 1e-8, (err, info)
+    assert info["rel_residual"] <= 1e-8
+
+
+def test_solve_matches_oracle_amen():
+    prob = W.plate_traction_smooth(4)
+    Ko, fo = assembly.assemble(prob)
+    x0, z0 = _x0z0(prob)
+    xo, io = amen.amen_solve(Ko, fo, x0, z0, 1e-9, max_sweeps=30, local_direct_max=2048)
+    K, f = q.qtt_assemble_stiffness(prob)
+    u, info = q.qtt_solve(K, f, q.QTT.from_cores(x0), q.QTT.from_cores(z0), tol=1e-9, max_sweeps=30,
+                          local_direct_max=2048)
+    assert info["rc"] == 0 and io.converged
+    ug = q.qtt_to_full(u).cpu().numpy()
+    uo = tt.full(xo)
+    assert np.linalg.norm(ug - uo) / np.linalg.norm(uo) <= 1e-7
+
+
+def test_solve_gmres_path():
+    """Force the iterative local solver (dense LU disabled)."""
+    prob = W.plate_body_force(4)
+    K, f = q.qtt_assemble_stiffness(prob)
+    u, info = q.qtt_solve(K, f, tol=1e-9, max_sweeps=40, local_direct_max=1, local_restart=40,
+                          local_max_cycles=20)
+    ug = q.qtt_to_full(u).cpu().numpy()
+    ref = fem.solve_duplicated(prob)
+    err = np.linalg.norm(ug - ref) / np.linalg.norm(ref)
+    assert err <= 1e-6, (err, info)
+
+
+def test_solve_mixed_precision_refinement():
+    prob = W.plate_body_force(5)
+    K, f = q.qtt_assemble_stiffness(prob)
+    u, info = q.qtt_solve(K, f, tol=1e-9, precision=q.QTT_MIXED, inner_tol=1e-4, refine_max=8, max_sweeps=30)
+    ug = q.qtt_to_full(u).cpu().numpy()
+    ref = fem.solve_duplicated(prob)
+    err = np.linalg.norm(ug - ref) / np.linalg.norm(ref)
+    assert info["rc"] == 0, info
+    assert info["rel_residual"] <= 1e-9
+    assert err <= 1e-7, (err, info)
