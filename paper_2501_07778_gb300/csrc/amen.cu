@@ -38,6 +38,29 @@ struct DBuf {
   T* p = nullptr;
   size_t cap = 0;
   cudaStream_t s = nullptr;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept : p(o.p), cap(o.cap), s(o.s) {
+    o.p = nullptr;
+    o.cap = 0;
+  }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) {
+      if (p) cudaFreeAsync(p, s);
+      p = o.p;
+      cap = o.cap;
+      s = o.s;
+      o.p = nullptr;
+      o.cap = 0;
+    }
+    return *this;
+  }
+  void swap(DBuf& o) noexcept {
+    std::swap(p, o.p);
+    std::swap(cap, o.cap);
+    std::swap(s, o.s);
+  }
   void ensure(size_t n, cudaStream_t st) {
     s = st;
     if (n <= cap) return;
@@ -455,10 +478,10 @@ struct Amen {
         left_XAX(z, x, k, ZAX_L.p, ZAX_Ln.p, sc);
         ZY_Ln.ensure((size_t)zk * ry(k + 1), s);
         left_XY(z, k, ZY_L.p, ZY_Ln.p, sc);
-        std::swap(XAX_L, XAX_Ln);
-        std::swap(XY_L, XY_Ln);
-        std::swap(ZAX_L, ZAX_Ln);
-        std::swap(ZY_L, ZY_Ln);
+        XAX_L.swap(XAX_Ln);
+        XY_L.swap(XY_Ln);
+        ZAX_L.swap(ZAX_Ln);
+        ZY_L.swap(ZY_Ln);
       }
       if (info) {
         info->sweeps += 1;
