@@ -227,6 +227,25 @@ int qtt_solve(const qtt_tensor* K, const qtt_tensor* f, const qtt_tensor* x0,
 int qtt_residual(const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* f,
                  double* out, void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Diagnostics (not part of the method)                                      */
+/* ------------------------------------------------------------------------ */
+
+/* Number of CUDA kernels this library has launched in this process. */
+unsigned long long qtt_kernel_launches(void);
+
+/* on != 0: bracket every launch of the profiled kernel classes with CUDA
+ * events on its stream and record its algorithmic flops and bytes (adds
+ * launch overhead; off by default).  Classes: 0 FP64 GEMM, 1 FP32 GEMM,
+ * 2 MPO x MPS core product, 3 Householder panel, 4 Jacobi SVD, 5 LU panel,
+ * 6 permutation, 7 full expansion. */
+int qtt_profile_enable(int on);
+
+/* Sum of event-timed milliseconds, algorithmic flops and bytes, and launch
+ * count of class cls (-1: all classes) recorded since the last read; waits
+ * for the recorded events and clears them. */
+int qtt_profile_read(int cls, double* ms, double* flops, double* bytes, long long* launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -62,6 +62,10 @@ SIGNATURES = {
     "qtt_to_full": (C.c_int, [P, P, C.c_size_t, C.c_int, P]),
     "qtt_solve": (C.c_int, [P, P, P, P, C.POINTER(QttSolveOpts), PP, C.POINTER(QttSolveInfo), P]),
     "qtt_residual": (C.c_int, [P, P, P, C.POINTER(C.c_double), P]),
+    "qtt_kernel_launches": (C.c_ulonglong, []),
+    "qtt_profile_enable": (C.c_int, [C.c_int]),
+    "qtt_profile_read": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                   C.POINTER(C.c_longlong)]),
 }
 
 _lib = None

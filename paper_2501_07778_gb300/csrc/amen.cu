@@ -152,6 +152,21 @@ __global__ void proxy_kernel(T* c, long long n, int k) {
     c[i] = (T)sin(0.7 + 1.3 * (double)i + 2.1 * (double)k + 0.37 * (double)(i * i % 97));
 }
 
+// (B x)[a,i,b] = sum PhiL[a,A,c] K_k[A,i,j,B] PhiR[b,B,d] x[c,j,d], contracted
+// over d, then (j, B), then (c, A); PhiL (ra,R0,rc), PhiR (rb,R1,rd), x (rc,n,rd)
+template <typename U>
+void apply_local(cudaStream_t s, Arena& sc, const U* PhiL, int ra, int rc, const U* Ak, int R0, int n, int R1,
+                 const U* PhiR, int rb, int rd, const U* xk, U* out) {
+  int dx[3] = {rc, n, rd}, dR[3] = {rb, R1, rd};
+  U* t1 = sc.alloc<U>((size_t)rc * n * rb * R1);
+  einsum<U>(s, sc, "cjd,bBd->cjbB", xk, dx, PhiR, dR, t1);
+  int d1[4] = {rc, n, rb, R1}, dA[4] = {R0, n, n, R1};
+  U* t2 = sc.alloc<U>((size_t)rc * rb * R0 * n);
+  einsum<U>(s, sc, "cjbB,AijB->cbAi", t1, d1, Ak, dA, t2);
+  int dL[3] = {ra, R0, rc}, d2[4] = {rc, rb, R0, n};
+  einsum<U>(s, sc, "aAc,cbAi->aib", PhiL, dL, t2, d2, out);
+}
+
 // ---------------------------------------------------------------------------
 // the solver
 // ---------------------------------------------------------------------------
@@ -166,6 +181,7 @@ struct Amen {
   int D;
   double tol;
   int max_rank, kick, max_sweeps, ndir, restart, cycles, verbose;
+  bool mixed_local = false;   // FP32 operator inside the local GMRES cycles
   // interfaces: PhiR[k] (bond k), k = 0..D
   std::vector<DBuf<T>> XAX_R, XY_R, ZAX_R, ZY_R;
   DBuf<T> XAX_L, XY_L, ZAX_L, ZY_L, XAX_Ln, XY_Ln, ZAX_Ln, ZY_Ln;
@@ -187,15 +203,7 @@ struct Amen {
 
   // (B x)[a,i,b] with B = PhiL (ra,R0,rc) K_k PhiR (rb,R1,rd), x (rc, n, rd)
   void local_apply(const T* PhiL, int ra, int rc, int k, const T* PhiR, int rb, int rd, const T* xk, T* out, Arena& sc) {
-    const int n = A->n[k], R0 = rA(k), R1 = rA(k + 1);
-    int dx[3] = {rc, n, rd}, dR[3] = {rb, R1, rd};
-    T* t1 = sc.alloc<T>((size_t)rc * n * rb * R1);
-    einsum<T>(s, sc, "cjd,bBd->cjbB", xk, dx, PhiR, dR, t1);
-    int d1[4] = {rc, n, rb, R1}, dA[4] = {R0, n, n, R1};
-    T* t2 = sc.alloc<T>((size_t)rc * rb * R0 * n);
-    einsum<T>(s, sc, "cjbB,AijB->cbAi", t1, d1, (const T*)A->core[k], dA, t2);
-    int dL[3] = {ra, R0, rc}, d2[4] = {rc, rb, R0, n};
-    einsum<T>(s, sc, "aAc,cbAi->aib", PhiL, dL, t2, d2, out);
+    apply_local<T>(s, sc, PhiL, ra, rc, (const T*)A->core[k], rA(k), A->n[k], rA(k + 1), PhiR, rb, rd, xk, out);
   }
 
   // g[a,i,b] = PsiL (ra, ryl) y_k (ryl, n, ryr) PsiR (rb, ryr)
@@ -282,55 +290,89 @@ struct Amen {
     }
   }
 
-  // restarted GMRES on the local operator; x holds the initial guess and
-  // receives the solution; returns the final relative residual estimate
+  // Restarted GMRES on the local operator with the residual of every cycle
+  // recomputed in T: x holds the initial guess and receives the solution.
+  // With U = float (mixed precision) each cycle runs its Arnoldi process on
+  // an FP32 copy of the local operator for the correction equation
+  // B d = g - B x, and x += d is accumulated in T (local iterative
+  // refinement); with U = T it is plain restarted GMRES.  Returns the final
+  // relative residual.
+  template <typename U>
   double gmres(int k, const T* PhiL, int r0, const T* PhiR, int r1, const T* g, double gn, T* xk, double rtol) {
-    const int n = A->n[k];
+    const int n = A->n[k], R0 = rA(k), R1 = rA(k + 1);
     const int N = r0 * n * r1;
     const int m = std::min(restart, N);
     Arena sc(s);
-    T* V = sc.alloc<T>((size_t)N * (m + 1));
-    T* w = sc.alloc<T>(N);
-    T* hcol = sc.alloc<T>(m + 1);
-    T* hcol2 = sc.alloc<T>(m + 1);
+    // operator in U
+    const U* PL = reinterpret_cast<const U*>(PhiL);
+    const U* PR = reinterpret_cast<const U*>(PhiR);
+    const U* Ak = reinterpret_cast<const U*>(A->core[k]);
+    if (sizeof(U) != sizeof(T)) {
+      U* a = sc.alloc<U>((size_t)r0 * R0 * r0);
+      convert<T, U>(s, PhiL, a, (size_t)r0 * R0 * r0);
+      U* b = sc.alloc<U>((size_t)r1 * R1 * r1);
+      convert<T, U>(s, PhiR, b, (size_t)r1 * R1 * r1);
+      U* c = sc.alloc<U>((size_t)R0 * n * n * R1);
+      convert<T, U>(s, (const T*)A->core[k], c, (size_t)R0 * n * n * R1);
+      PL = a;
+      PR = b;
+      Ak = c;
+    }
+    U* V = sc.alloc<U>((size_t)N * (m + 1));
+    U* w = sc.alloc<U>(N);
+    U* hcol = sc.alloc<U>(m + 1);
+    U* hcol2 = sc.alloc<U>(m + 1);
     double* H = sc.alloc<double>((size_t)(m + 1) * m);
     double* yv = sc.alloc<double>(m);
-    T* yT = sc.alloc<T>(m);
+    U* yU = sc.alloc<U>(m);
+    U* dU = sc.alloc<U>(N);
+    T* wT = sc.alloc<T>(N);
     double* dres = sc.alloc<double>(1);
     double* hlast = sc.alloc<double>(1);
     double rel = 1.0;
     for (int cyc = 0; cyc < cycles; ++cyc) {
       Arena it(s);
-      // r0 = g - B x
-      local_apply(PhiL, r0, r0, k, PhiR, r1, r1, xk, w, it);
-      axpby<T>(s, N, T(1), g, T(-1), w);        // w = g - Bx
-      double beta = host_norm(w, N);
+      // residual in T: wT = g - B x
+      local_apply(PhiL, r0, r0, k, PhiR, r1, r1, xk, wT, it);
+      axpby<T>(s, N, T(1), g, T(-1), wT);
+      double beta = host_norm(wT, N);
       rel = gn > 0 ? beta / gn : beta;
       if (rel <= rtol || beta == 0.0) break;
       QTT_CUDA(cudaMemsetAsync(H, 0, sizeof(double) * (m + 1) * m, s));
-      sumsq<T>(s, w, N, dscal);
-      scale_by_device_kernel<T><<<grid_for(N), 256, 0, s>>>(V, w, N, dscal, nullptr);
+      sumsq<T>(s, wT, N, dscal);
+      if (sizeof(U) != sizeof(T)) {
+        convert<T, U>(s, wT, w, N);
+        scale_by_device_kernel<U><<<grid_for(N), 256, 0, s>>>(V, w, N, dscal, nullptr);
+      } else {
+        scale_by_device_kernel<U><<<grid_for(N), 256, 0, s>>>(V, reinterpret_cast<const U*>(wT), N, dscal, nullptr);
+      }
       QTT_CHECK_LAUNCH();
       for (int j = 0; j < m; ++j) {
         Arena ij(s);
-        local_apply(PhiL, r0, r0, k, PhiR, r1, r1, V + (size_t)N * j, w, ij);
+        apply_local<U>(s, ij, PL, r0, r0, Ak, R0, n, R1, PR, r1, r1, V + (size_t)N * j, w);
         // classical Gram-Schmidt, twice
-        gemm<T>(s, true, false, j + 1, 1, N, T(1), V, N, 0, w, N, 0, T(0), hcol, j + 1, 0);
-        gemm<T>(s, false, false, N, 1, j + 1, T(-1), V, N, 0, hcol, j + 1, 0, T(1), w, N, 0);
-        gemm<T>(s, true, false, j + 1, 1, N, T(1), V, N, 0, w, N, 0, T(0), hcol2, j + 1, 0);
-        gemm<T>(s, false, false, N, 1, j + 1, T(-1), V, N, 0, hcol2, j + 1, 0, T(1), w, N, 0);
-        axpby<T>(s, j + 1, T(1), hcol2, T(1), hcol);
-        sumsq<T>(s, w, N, dscal);
-        scale_by_device_kernel<T><<<grid_for(N), 256, 0, s>>>(V + (size_t)N * (j + 1), w, N, dscal, hlast);
+        gemm<U>(s, true, false, j + 1, 1, N, U(1), V, N, 0, w, N, 0, U(0), hcol, j + 1, 0);
+        gemm<U>(s, false, false, N, 1, j + 1, U(-1), V, N, 0, hcol, j + 1, 0, U(1), w, N, 0);
+        gemm<U>(s, true, false, j + 1, 1, N, U(1), V, N, 0, w, N, 0, U(0), hcol2, j + 1, 0);
+        gemm<U>(s, false, false, N, 1, j + 1, U(-1), V, N, 0, hcol2, j + 1, 0, U(1), w, N, 0);
+        axpby<U>(s, j + 1, U(1), hcol2, U(1), hcol);
+        sumsq<U>(s, w, N, dscal);
+        scale_by_device_kernel<U><<<grid_for(N), 256, 0, s>>>(V + (size_t)N * (j + 1), w, N, dscal, hlast);
         QTT_CHECK_LAUNCH();
-        store_col_kernel<T><<<(m + 128) / 128, 128, 0, s>>>(H, m + 1, j, hcol, j + 1, hlast);
+        store_col_kernel<U><<<(m + 128) / 128, 128, 0, s>>>(H, m + 1, j, hcol, j + 1, hlast);
         QTT_CHECK_LAUNCH();
       }
       gmres_lsq_kernel<<<1, 1, 0, s>>>(H, m, beta, yv, dres);
       QTT_CHECK_LAUNCH();
-      to_T_kernel<T><<<(m + 127) / 128, 128, 0, s>>>(yv, yT, m);
+      to_T_kernel<U><<<(m + 127) / 128, 128, 0, s>>>(yv, yU, m);
       QTT_CHECK_LAUNCH();
-      gemm<T>(s, false, false, N, 1, m, T(1), V, N, 0, yT, m, 0, T(1), xk, N, 0);
+      gemm<U>(s, false, false, N, 1, m, U(1), V, N, 0, yU, m, 0, U(0), dU, N, 0);
+      if (sizeof(U) != sizeof(T)) {
+        convert<U, T>(s, dU, wT, N);
+        axpby<T>(s, N, T(1), wT, T(1), xk);
+      } else {
+        axpby<T>(s, N, T(1), reinterpret_cast<const T*>(dU), T(1), xk);
+      }
       if (info) info->local_iters += m;
     }
     return rel;
@@ -389,7 +431,8 @@ struct Amen {
           lu_solve<T>(s, sc, N, Bm, N, sol, N, 1, dinfo);
         } else {
           QTT_CUDA(cudaMemcpyAsync(sol, xk, sizeof(T) * N, cudaMemcpyDeviceToDevice, s));
-          gmres(k, XAX_L.p, r0, PhiR, r1, g, gn, sol, delta);
+          if (mixed_local && sizeof(T) == 8) gmres<float>(k, XAX_L.p, r0, PhiR, r1, g, gn, sol, delta);
+          else gmres<T>(k, XAX_L.p, r0, PhiR, r1, g, gn, sol, delta);
         }
         if (info) info->local_solves += 1;
         if (k == D - 1) {
@@ -532,7 +575,7 @@ Tptr default_z0(cudaStream_t s, const qtt_tensor* f, int rho, int prec) {
 
 template <typename T>
 int amen_run(cudaStream_t s, const qtt_tensor* K, const qtt_tensor* f, qtt_tensor* x, qtt_tensor* z, double tol,
-             const qtt_solve_opts& o, qtt_solve_info* info) {
+             const qtt_solve_opts& o, qtt_solve_info* info, bool mixed_local = false) {
   Arena ar(s);
   Amen<T> am(s, ar);
   am.A = K;
@@ -549,6 +592,7 @@ int amen_run(cudaStream_t s, const qtt_tensor* K, const qtt_tensor* f, qtt_tenso
   am.cycles = o.local_max_cycles > 0 ? o.local_max_cycles : 8;
   am.verbose = o.verbose;
   am.info = info;
+  am.mixed_local = mixed_local;
   am.dscal = ar.alloc<double>(4);
   int rc = am.run();
   QTT_CUDA(cudaStreamSynchronize(s));
@@ -609,28 +653,27 @@ int solve(const qtt_tensor* K, const qtt_tensor* f, const qtt_tensor* x0, const 
   } else {
     QTT_REQUIRE(o.precision == QTT_MIXED, "qtt_solve: unknown precision");
     QTT_REQUIRE(K->prec == QTT_F64 && f->prec == QTT_F64, "qtt_solve: mixed precision needs FP64 K and f");
-    const double inner = o.inner_tol > 0 ? o.inner_tol : 1e-5;
-    const int refine_max = o.refine_max > 0 ? o.refine_max : 6;
-    auto K32 = own(tensor_clone(K, QTT_F32, s));
-    Tptr u = x0 ? own(tensor_clone(x0, QTT_F64, s)) : own(nullptr);
-    Tptr z = z0 ? own(tensor_clone(z0, QTT_F32, s)) : default_z0(s, f, rho, QTT_F32);
+    // Sweeps with FP64 interfaces and local residuals; the Krylov cycles of
+    // every local solve apply an FP32 copy of the local operator (local
+    // iterative refinement).  Then the FP64 global residual r = f - K u
+    // (QTT matvec and sum in FP64) decides; if it is above tol, r is rounded
+    // in FP64, K d = r is solved the same way and u <- round64(u + d).
+    const double inner = o.inner_tol > 0 ? o.inner_tol : 1e-3;
+    const int refine_max = o.refine_max > 0 ? o.refine_max : 4;
+    Tptr u = x0 ? own(tensor_clone(x0, QTT_F64, s)) : default_x0(s, f, QTT_F64);
+    Tptr z = z0 ? own(tensor_clone(z0, QTT_F64, s)) : default_z0(s, f, rho, QTT_F64);
+    rc = amen_run<double>(s, K, f, u.get(), z.get(), o.tol, o, inf, true);
     const double fn = [&] {
       Arena ar(s);
       return norm<double>(s, ar, f);
     }();
-    rc = QTT_ENOCONV;
-    for (int it = 0; it <= refine_max; ++it) {
-      // r = f - K u  (FP64 matvec, FP64 rounding)
+    for (int it = 0;; ++it) {
       Tptr r = own(nullptr);
       double rel = 1.0;
       {
         Arena ar(s);
-        if (u) {
-          auto Ku = own(product<double>(s, K, u.get()));
-          r = own(tt_sum<double>(s, 1.0, f, -1.0, Ku.get()));
-        } else {
-          r = own(tensor_clone(f, QTT_F64, s));
-        }
+        auto Ku = own(product<double>(s, K, u.get()));
+        r = own(tt_sum<double>(s, 1.0, f, -1.0, Ku.get()));
         left_orthogonalize<double>(s, ar, r.get(), r->d - 1);
         double* dv = ar.alloc<double>(1);
         sumsq<double>(s, (const double*)r->core[r->d - 1], core_elems(r.get(), r->d - 1), dv);
@@ -639,27 +682,22 @@ int solve(const qtt_tensor* K, const qtt_tensor* f, const qtt_tensor* x0, const 
         QTT_CUDA(cudaStreamSynchronize(s));
         rel = std::sqrt(rn2) / (fn > 0 ? fn : 1.0);
         inf->rel_residual = rel;
-        if (o.verbose) fprintf(stderr, "[qtt_solve mixed] refinement %d: rel residual %.3e\n", it, rel);
-        if (rel <= o.tol || it == refine_max) {
+        if (o.verbose) fprintf(stderr, "[qtt_solve mixed] check %d: FP64 rel residual %.3e\n", it, rel);
+        if (rel <= o.tol || it >= refine_max) {
           rc = rel <= o.tol ? QTT_OK : QTT_ENOCONV;
           break;
         }
-        round_tt<double>(s, ar, r.get(), std::min(1e-2, 0.1 * inner), 0);
+        // the sweep above left r's cores left-orthogonal: round them in FP64
+        round_tt<double>(s, ar, r.get(), std::min(1e-2, inner), 0);
       }
-      auto r32 = own(tensor_clone(r.get(), QTT_F32, s));
-      auto d32 = default_x0(s, f, QTT_F32);
-      amen_run<float>(s, K32.get(), r32.get(), d32.get(), z.get(), inner, o, inf);
-      auto d64 = own(tensor_clone(d32.get(), QTT_F64, s));
-      if (!u) {
-        u = std::move(d64);
-      } else {
-        u = own(tt_sum<double>(s, 1.0, u.get(), 1.0, d64.get()));
-      }
+      auto d = default_x0(s, f, QTT_F64);
+      auto zd = default_z0(s, f, rho, QTT_F64);
+      amen_run<double>(s, K, r.get(), d.get(), zd.get(), inner, o, inf, true);
+      u = own(tt_sum<double>(s, 1.0, u.get(), 1.0, d.get()));
       Arena ar(s);
       round_tt<double>(s, ar, u.get(), std::max(1e-15, 1e-3 * o.tol), o.max_rank > 0 ? o.max_rank : 0);
       inf->refinements += 1;
     }
-    if (!u) u = default_x0(s, f, QTT_F64);
     *xout = u.release();
   }
   inf->status = rc;

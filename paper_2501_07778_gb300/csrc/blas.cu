@@ -17,16 +17,21 @@ namespace qtt {
 namespace {
 constexpr int GBM = 64, GBN = 64, GBK = 16;
 
+// gridDim.z = batch * splits: a split computes the partial product over
+// K range [split * kchunk, min(K, (split + 1) * kchunk)) and, when splits > 1,
+// adds alpha * partial into C atomically (C pre-scaled by beta on the host side).
 template <typename T>
 __global__ void __launch_bounds__(256) gemm_kernel(bool tA, bool tB, int M, int N, int K, T alpha, const T* __restrict__ A,
                                                   int lda, long long sA, const T* __restrict__ B, int ldb,
-                                                  long long sB, T beta, T* __restrict__ C, int ldc, long long sC) {
+                                                  long long sB, T beta, T* __restrict__ C, int ldc, long long sC,
+                                                  int splits, int kchunk) {
   __shared__ T As[GBK][GBM + 1];
   __shared__ T Bs[GBK][GBN + 1];
-  const int bz = blockIdx.z;
+  const int bz = blockIdx.z / splits, sp = blockIdx.z % splits;
   A += bz * sA;
   B += bz * sB;
   C += bz * sC;
+  const int kb = sp * kchunk, ke = min(K, kb + kchunk);
   const int m0 = blockIdx.x * GBM, n0 = blockIdx.y * GBN;
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
@@ -35,7 +40,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(bool tA, bool tB, int M, int 
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-  for (int k0 = 0; k0 < K; k0 += GBK) {
+  for (int k0 = kb; k0 < ke; k0 += GBK) {
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       int L = tid + 256 * t;
@@ -43,13 +48,13 @@ __global__ void __launch_bounds__(256) gemm_kernel(bool tA, bool tB, int M, int 
       if (!tA) { i = L % GBM; k = L / GBM; } else { k = L % GBK; i = L / GBK; }
       int gi = m0 + i, gk = k0 + k;
       T v = T(0);
-      if (gi < M && gk < K) v = tA ? A[gk + (long long)gi * lda] : A[gi + (long long)gk * lda];
+      if (gi < M && gk < ke) v = tA ? A[gk + (long long)gi * lda] : A[gi + (long long)gk * lda];
       As[k][i] = v;
       int j, kk;
       if (!tB) { kk = L % GBK; j = L / GBK; } else { j = L % GBN; kk = L / GBN; }
       int gj = n0 + j, gk2 = k0 + kk;
       T w = T(0);
-      if (gj < N && gk2 < K) w = tB ? B[gj + (long long)gk2 * ldb] : B[gk2 + (long long)gj * ldb];
+      if (gj < N && gk2 < ke) w = tB ? B[gj + (long long)gk2 * ldb] : B[gk2 + (long long)gj * ldb];
       Bs[kk][j] = w;
     }
     __syncthreads();
@@ -76,8 +81,22 @@ __global__ void __launch_bounds__(256) gemm_kernel(bool tA, bool tB, int M, int 
       int gj = n0 + ty + 16 * j;
       if (gj >= N) continue;
       T* c = C + gi + (long long)gj * ldc;
-      *c = (beta == T(0)) ? alpha * acc[i][j] : alpha * acc[i][j] + beta * (*c);
+      if (splits > 1) atomicAdd(c, alpha * acc[i][j]);
+      else *c = (beta == T(0)) ? alpha * acc[i][j] : alpha * acc[i][j] + beta * (*c);
     }
+  }
+}
+
+template <typename T>
+__global__ void scale_matrix_kernel(int M, int N, T* C, int ldc, long long sC, int batch, T beta) {
+  long long total = (long long)M * N * batch;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(t % M);
+    long long r = t / M;
+    int j = (int)(r % N), b = (int)(r / N);
+    T* c = C + b * sC + i + (long long)j * ldc;
+    *c = (beta == T(0)) ? T(0) : beta * (*c);
   }
 }
 
@@ -178,10 +197,35 @@ void gemm(cudaStream_t s, bool tA, bool tB, int M, int N, int K, T alpha, const 
     }
     return;
   }
-  dim3 grid((M + GBM - 1) / GBM, (N + GBN - 1) / GBN, batch);
+  // split K when the output tiles alone cannot fill the 152 SMs twice over
+  const long long tiles = (long long)((M + GBM - 1) / GBM) * ((N + GBN - 1) / GBN) * batch;
+  int splits = 1;
+  if (tiles < 304 && K >= 256) {
+    long long want = (304 + tiles - 1) / tiles;
+    splits = (int)std::min<long long>(want, (K + 127) / 128);
+    splits = std::max(1, std::min(splits, 65535 / std::max(1, batch)));
+  }
+  int kchunk = K;
+  if (splits > 1) {
+    kchunk = ((K + splits - 1) / splits + GBK - 1) / GBK * GBK;
+    splits = (K + kchunk - 1) / kchunk;
+  }
+  dim3 grid((M + GBM - 1) / GBM, (N + GBN - 1) / GBN, batch * splits);
   QTT_REQUIRE(grid.y <= 65535 && grid.z <= 65535, "gemm grid too large");
-  gemm_kernel<T><<<grid, 256, 0, s>>>(tA, tB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+  ProfToken pt = prof_begin(sizeof(T) == 8 ? PROF_GEMM_F64 : PROF_GEMM_F32, s);
+  if (splits > 1) {
+    long long total = (long long)M * N * batch;
+    scale_matrix_kernel<T><<<grid_for(total), 256, 0, s>>>(M, N, C, ldc, sC, batch, beta);
+    QTT_CHECK_LAUNCH();
+  }
+  gemm_kernel<T><<<grid, 256, 0, s>>>(tA, tB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits,
+                                      kchunk);
   QTT_CHECK_LAUNCH();
+  if (pt.ev) {
+    const double mn = (double)M * N, b = (double)batch;
+    prof_end(pt, s, 2.0 * mn * K * b,
+             b * sizeof(T) * ((double)M * K + (double)K * N + (beta == T(0) ? 1.0 : 2.0) * mn));
+  }
 }
 
 template <typename T>
@@ -201,8 +245,10 @@ void permute(cudaStream_t s, const T* in, T* out, int nd, const int* dims, const
     total *= dims[k];
   }
   if (total == 0) return;
+  ProfToken pt = prof_begin(PROF_PERMUTE, s);
   permute_kernel<T><<<grid_for(total), 256, 0, s>>>(in, out, total, a, alpha, beta);
   QTT_CHECK_LAUNCH();
+  if (pt.ev) prof_end(pt, s, 0.0, (double)total * sizeof(T) * (beta == T(0) ? 2.0 : 3.0));
 }
 
 template <typename T>

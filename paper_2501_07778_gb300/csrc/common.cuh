@@ -34,7 +34,25 @@ void set_last_error(const std::string& msg);
     }                                                                               \
   } while (0)
 
-#define QTT_CHECK_LAUNCH() QTT_CUDA(cudaGetLastError())
+// every kernel launch of the library is followed by this check, which also
+// counts the launch (qtt_kernel_launches)
+void count_launch();
+#define QTT_CHECK_LAUNCH()       \
+  do {                           \
+    ::qtt::count_launch();       \
+    QTT_CUDA(cudaGetLastError()); \
+  } while (0)
+
+// Per-kernel-class CUDA-event timing, active after qtt_profile_enable(1).
+enum ProfClass { PROF_GEMM_F64 = 0, PROF_GEMM_F32 = 1, PROF_CORE_PRODUCT = 2, PROF_QR_PANEL = 3, PROF_JACOBI = 4,
+                 PROF_LU_PANEL = 5, PROF_PERMUTE = 6, PROF_TO_FULL = 7, PROF_NCLASS = 8 };
+struct ProfToken {
+  int cls;
+  cudaEvent_t ev;
+};
+bool prof_on();
+ProfToken prof_begin(int cls, cudaStream_t s);
+void prof_end(const ProfToken& t, cudaStream_t s, double flops, double bytes);
 
 #define QTT_REQUIRE(cond, msg)                                             \
   do {                                                                     \

@@ -355,8 +355,10 @@ void qr(cudaStream_t s, Arena& ar, int m, int n, T* A, int lda, T* Q, int ldq, T
     if (j0 > 0) {
       for (int c = 0; c < jb; ++c) QTT_CUDA(cudaMemsetAsync(Vall + (long long)(j0 + c) * m, 0, sizeof(T) * j0, s));
     }
+    ProfToken pt = prof_begin(PROF_QR_PANEL, s);
     qr_panel_kernel<T><<<1, PT, 0, s>>>(mm, jb, A + j0 + (long long)j0 * lda, lda, Vb, m, Tb);
     QTT_CHECK_LAUNCH();
+    if (pt.ev) prof_end(pt, s, 4.0 * mm * jb * jb, sizeof(T) * 3.0 * mm * jb);
     const int n2 = n - j0 - jb;
     if (n2 > 0) {
       T* C = A + j0 + (long long)(j0 + jb) * lda;
@@ -419,8 +421,11 @@ void svd(cudaStream_t s, Arena& ar, int m, int n, T* A, int lda, T* U, int ldu, 
   T* Vm = ar.alloc<T>((size_t)n * n);
   set_identity_kernel<T><<<grid_for((long long)n * n), 256, 0, s>>>(Vm, n, n, n);
   QTT_CHECK_LAUNCH();
+  ProfToken pj = prof_begin(PROF_JACOBI, s);
   jacobi_kernel<T><<<1, 1024, 0, s>>>(k, n, R, k, Vm, n, 40, nullptr);
   QTT_CHECK_LAUNCH();
+  // nominal work of one sweep over all pairs (the sweep count is data dependent)
+  if (pj.ev) prof_end(pj, s, 0.5 * n * (n - 1) * (6.0 * k + 12.0 * k + 12.0 * n), sizeof(T) * 2.0 * (k + n) * n);
   int* order = ar.alloc<int>(n);
   svd_finish_kernel<T><<<1, 1024, sizeof(double) * n, s>>>(k, n, R, k, S, order);
   QTT_CHECK_LAUNCH();
@@ -440,8 +445,10 @@ void lu_solve(cudaStream_t s, Arena& ar, int n, T* A, int lda, T* B, int ldb, in
   if (info) QTT_CUDA(cudaMemsetAsync(info, 0, sizeof(int), s));
   for (int j0 = 0; j0 < n; j0 += NB) {
     const int jb = std::min(NB, n - j0);
+    ProfToken pl = prof_begin(PROF_LU_PANEL, s);
     lu_panel_kernel<T><<<1, PT, 0, s>>>(n, j0, jb, A, lda, B, ldb, nrhs, info);
     QTT_CHECK_LAUNCH();
+    if (pl.ev) prof_end(pl, s, 1.0 * (n - j0) * jb * jb, sizeof(T) * 2.0 * (n - j0) * jb);
     const int n2 = n - j0 - jb;
     if (n2 > 0) {
       T* L11 = A + j0 + (long long)j0 * lda;

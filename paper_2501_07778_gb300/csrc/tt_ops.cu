@@ -166,8 +166,13 @@ template <typename T>
 void core_product(cudaStream_t s, int R0, int n, int mm, int R1, int r0, int p, int r1, const T* A, const T* X, T* Y) {
   long long total = (long long)R0 * r0 * n * p * R1 * r1;
   if (total == 0) return;
+  ProfToken pt = prof_begin(PROF_CORE_PRODUCT, s);
   core_product_kernel<T><<<grid_for(total), 256, 0, s>>>(R0, n, mm, R1, r0, p, r1, A, X, Y, total);
   QTT_CHECK_LAUNCH();
+  // algorithmic traffic: read both cores once, write the product core
+  if (pt.ev)
+    prof_end(pt, s, 2.0 * (double)total * mm,
+             sizeof(T) * ((double)total + (double)R0 * n * mm * R1 + (double)r0 * mm * p * r1));
 }
 
 // ---------------------------------------------------------------------------
