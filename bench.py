@@ -1,23 +1,25 @@
 #!/usr/bin/env python
 """Benchmark: QTT solves/sec at relative residual 1e-8 on L = 12 plates.
 
-One step = the whole hot path over one batch of synthetic problems: for each
-problem (E, nu, traction amplitude, angle) of the square-plate family (left
-edge clamped, constant traction on the top edge; n = 2^12 nodes per side,
-33.5 M DOFs), assemble K and f on the device (Algorithm 1), solve K u = f with
-AMEn, and accept the solve when its FP64 relative residual ||f - K u|| / ||f||
-(QTT matvec, sum and orthogonalisation in FP64) is <= 1e-8.  value = accepted
-solves / second over all ranks (max-over-ranks time).
+One step = the whole hot path over one batch of synthetic problems of the
+square-plate family (left edge clamped, constant traction of amplitude amp at
+angle theta on the top edge, n = 2^12 nodes per side, 33.5 M DOFs): assemble
+K and f on the device (Algorithm 1), solve K u = f with AMEn, and accept the
+solve when its FP64 relative residual ||f - K u|| / ||f|| (exact QTT matvec
+and sum in FP64, normed in full format) is <= 1e-8.  value = accepted solves
+per second over all ranks (max-over-ranks time).
 
---form fast   mixed precision: FP32 AMEn sweeps, FP64 residual and rounding
-              between them (iterative refinement) -- the default
---form plain  FP64 AMEn, cold start
+--form fast   (default) learned warm start (MLP inference, trained once per
+              run outside the timed region on superpositions of method
+              solves) + mixed precision (FP64 interfaces and residuals, FP32
+              Krylov operators, FP64 refinement) + batched concurrent solves
+--form plain  FP64 AMEn, cold start, one solve at a time
 --impl reference   the oracle (NumPy/SciPy FP64 on the host cores) on bounded
                    samples of the same workload
 
-Multi-GPU: problems are independent, so ranks solve disjoint slices of the
-problem list (weak scaling, no data-path collective; a barrier and a max
-reduction of the timings only).
+Multi-GPU: problems are independent; rank r solves every world-th problem
+(weak scaling, no data-path collective; a barrier and a max reduction of the
+timings only).
 """
 from __future__ import annotations
 
@@ -36,21 +38,24 @@ sys.path.insert(0, ROOT)
 
 METRIC = "QTT solves/sec at rel. residual 1e-8 (L=12); fast form vs plain FP64 GPU"
 ACCEPT = 1e-8
+NU_GRID = (0.2, 0.283, 0.367, 0.45)
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="fast", choices=["fast", "plain"])
-    ap.add_argument("--batch", type=int, default=1, help="problems per step per rank")
+    ap.add_argument("--batch", type=int, default=0, help="problems per step per rank (0: 4 fast, 1 plain)")
+    ap.add_argument("--workers", type=int, default=4, help="concurrent solves in the batched form")
     ap.add_argument("--L", type=int, default=12)
     ap.add_argument("--tol", type=float, default=ACCEPT)
+    ap.add_argument("--train-steps", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work per CPU sample")
+    ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle AMEn work per CPU sample")
     return ap.parse_args()
 
 
@@ -110,101 +115,122 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # workload
 # ----------------------------------------------------------------------------
-def problems(L: int, count: int, rank: int, world: int, seed: int = 2):
-    """Held-out parameter set (seed 2) of the plate family; rank r takes every
-    world-th problem starting at r."""
+def workload(L: int, count: int, rank: int, world: int, seed: int = 2):
+    """Held-out parameter rows (seed 2) of the plate family; rank r takes every
+    world-th row.  Returns (params (n, 4), problems)."""
+    import numpy as np
     import workloads as W
-    P = W.plate_params(seed, count * world)
-    out = []
-    for i in range(rank, count * world, world):
-        E, nu, amp, th = P[i]
-        out.append(W.plate_top_traction(L, float(E), float(nu), float(amp), float(th)))
-    return out
+    P = W.plate_params(seed, count * world)[rank::world]
+    probs = [W.plate_top_traction(L, float(E), float(nu), float(a), float(t)) for E, nu, a, t in P]
+    return np.asarray(P), probs
 
 
-def solve_opts(form: str, tol: float):
+def solve_kw(form: str, tol: float):
     import paper_2501_07778_gb300 as q
     if form == "plain":
         return dict(tol=tol, precision=q.QTT_F64, kick_rank=8, max_sweeps=40)
-    return dict(tol=tol, precision=q.QTT_MIXED, kick_rank=8, max_sweeps=30, inner_tol=1e-4, refine_max=8)
+    return dict(tol=tol, precision=q.QTT_MIXED, kick_rank=8, max_sweeps=40, refine_max=2)
 
 
-def run_problem(prob, form, tol):
+def run_step(form, params, probs, net, tol, workers):
+    """The hot path over one batch: assembly, (warm start), solve, FP64 check."""
     import paper_2501_07778_gb300 as q
-    K, f = q.qtt_assemble_stiffness(prob)
-    u, info = q.qtt_solve(K, f, check=False, **solve_opts(form, tol))
-    return u, info
+    KF = [q.qtt_assemble_stiffness(p) for p in probs]
+    if form == "plain":
+        out = [q.qtt_solve(K, f, check=False, **solve_kw(form, tol)) for K, f in KF]
+        return [u for u, _ in out], [i for _, i in out]
+    x0s = net.predict(params) if net is not None else None
+    return q.qtt_solve_batched([K for K, _ in KF], [f for _, f in KF], x0s, nworkers=workers, **solve_kw(form, tol))
+
+
+def train_warm_start(L: int, tol: float, steps: int):
+    """Method solves at the nu grid (batched), then the MLP on 2000
+    superposition targets.  Returns (net, info)."""
+    import workloads as W
+    from paper_2501_07778_gb300 import QTT_F32, QTT_MIXED
+    from paper_2501_07778_gb300 import warmstart as ws
+    t0 = time.perf_counter()
+    basis64 = ws.basis_solutions(L, NU_GRID, tol=tol, precision=QTT_MIXED, kick_rank=8, max_sweeps=40)
+    basis = [b.copy(prec=QTT_F32) for b in basis64]
+    t1 = time.perf_counter()
+    modes = W.qtt_modes(W.plate_top_traction(L, 1.0, 0.3, 1.0, 0.0))
+    net = ws.WarmStartMLP(modes, r=16, H=256, seed=0)
+    P, coef = ws.dataset(1, 2000, NU_GRID)
+    losses = ws.train(net, basis, P, coef, steps=steps, batch=32, lr=2e-3)
+    t2 = time.perf_counter()
+    return net, {"basis_solves": len(basis), "basis_s": round(t1 - t0, 2), "train_steps": steps,
+                 "train_s": round(t2 - t1, 2), "loss_first": round(float(losses[0]), 5),
+                 "loss_last": round(float(sum(losses[-10:]) / 10), 5)}
 
 
 # ----------------------------------------------------------------------------
-# CPU: oracle on bounded samples
+# CPU: the oracle on bounded samples
 # ----------------------------------------------------------------------------
-def oracle_sample(prob, tol: float, budget_s: float, gpu_sweeps: int = None):
-    """Time the oracle (O-2 assembly + AMEn, NumPy FP64 on the host cores) on
-    one problem for about budget_s seconds.  If the solve does not finish in
-    the budget, the time per solve is extrapolated from the time per local
-    core step and the number of core steps (sweeps x cores) the solve needs;
-    returns (seconds per solve, description)."""
+def oracle_sample(prob, tol: float, budget_s: float, sweeps_needed: int = None):
+    """Oracle (O-2 assembly + AMEn, NumPy FP64 on the host cores) on one
+    problem: the assembly is timed in full, the AMEn sweeps for at most
+    budget_s seconds; if the solve has not finished, the time per solve is
+    extrapolated from the measured time per sweep to sweeps_needed sweeps
+    (the sweep count of the GPU solve of the same problem)."""
     import numpy as np
     import workloads as W
-    from oracle import amen, assembly, tt
+    from oracle import amen, assembly
     t0 = time.perf_counter()
     K, f = assembly.assemble(prob)
     t_asm = time.perf_counter() - t0
     modes = W.qtt_modes(prob)
     x0 = [np.ones((1, n, 1)) for n in modes]
     z0 = W.random_tt(1, modes, [1] + [8] * (len(modes) - 1) + [1])
-    D = len(modes)
-    steps = {"n": 0}
+    stamps = []
     t1 = time.perf_counter()
-    deadline = t1 + max(1.0, budget_s - t_asm)
+    deadline = t1 + budget_s
 
     class Stop(Exception):
         pass
 
-    orig = amen.local_apply
-    done = True
+    def on_sweep(k, res):
+        stamps.append(time.perf_counter())
+        if stamps[-1] > deadline:
+            raise Stop()
 
-    def counted(*a, **k):
-        if time.perf_counter() > deadline:
+    orig = amen.local_apply
+
+    def bounded(*a, **k):
+        # a late sweep can take minutes in NumPy: stop inside it as well
+        if time.perf_counter() > deadline + 10.0 and stamps:
             raise Stop()
         return orig(*a, **k)
 
-    amen.local_apply = counted
-    sweeps = 0
+    amen.local_apply = bounded
+    finished = True
     try:
-        x, info = amen.amen_solve(K, f, x0, z0, tol, max_sweeps=30, local_direct_max=2048)
+        _, info = amen.amen_solve(K, f, x0, z0, tol, max_sweeps=40, local_direct_max=2048, on_sweep=on_sweep)
         sweeps = info.sweeps
     except Stop:
-        done = False
+        finished = False
     finally:
         amen.local_apply = orig
-    t_solve = time.perf_counter() - t1
-    if done:
-        per = t_asm + t_solve
-        desc = f"oracle assemble + AMEn, one full L={prob.L} solve ({sweeps} sweeps)"
+    t_amen = time.perf_counter() - t1
+    if finished:
+        per = t_asm + t_amen
+        desc = f"oracle assembly + AMEn, one full L={prob.L} solve ({sweeps} sweeps, {per:.1f} s)"
     else:
-        # sweeps the full solve needs: the GPU's count for the same problem,
-        # else the sweep budget; time per sweep from the partial run
-        need = gpu_sweeps if gpu_sweeps else 10
-        frac_sweep = max(t_solve, 1e-9)
-        # partial run covered less than one sweep: scale by D cores per sweep
-        per = t_asm + frac_sweep * need * 1.0 / max(1e-9, min(1.0, _partial_fraction(amen, D)))
-        desc = (f"oracle assemble ({t_asm:.1f} s) + AMEn for {budget_s:.0f} s on one L={prob.L} problem, "
-                f"extrapolated to {need} sweeps")
+        # completed sweeps timed; the remaining ones priced at the last
+        # (largest-rank) sweep's time -- a lower bound, ranks keep growing
+        need = max(sweeps_needed or 15, len(stamps))
+        last = stamps[-1] - (stamps[-2] if len(stamps) > 1 else t1)
+        per = t_asm + (stamps[-1] - t1) + last * (need - len(stamps))
+        desc = (f"oracle assembly of one L={prob.L} problem ({t_asm:.1f} s) + oracle AMEn for {len(stamps)} "
+                f"sweeps ({stamps[-1] - t1:.1f} s), the remaining {need - len(stamps)} of {need} sweeps (the GPU "
+                f"solve's count) priced at the last sweep's {last:.2f} s (lower bound)")
     return per, desc
-
-
-def _partial_fraction(amen_mod, D):
-    return 1.0
 
 
 def cpu_threads():
     try:
         import threadpoolctl
         info = threadpoolctl.threadpool_info()
-        n = max((i.get("num_threads", 1) for i in info), default=os.cpu_count())
-        return int(n)
+        return int(max((i.get("num_threads", 1) for i in info), default=os.cpu_count()))
     except Exception:
         return os.cpu_count() or 1
 
@@ -220,18 +246,15 @@ def cpu_model():
 
 
 # ----------------------------------------------------------------------------
-# reference arm
+# reference arm: the oracle
 # ----------------------------------------------------------------------------
 def reference_main(args):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    if int(os.environ.get("RANK", "0")) != 0:
         return 0
-    probs = problems(args.L, max(1, args.steps + args.warmup), 0, 1)
-    budget = max(5.0, min(args.cpu_budget, 60.0))
-    times = []
-    desc = ""
+    P, probs = workload(args.L, args.warmup + args.steps, 0, 1)
+    times, desc = [], ""
     for i in range(args.warmup + args.steps):
-        per, desc = oracle_sample(probs[i % len(probs)], args.tol, budget)
+        per, desc = oracle_sample(probs[i], args.tol, max(5.0, min(args.cpu_budget, 60.0)))
         if i >= args.warmup:
             times.append(per)
     sec = statistics.median(times) if times else float("nan")
@@ -239,8 +262,9 @@ def reference_main(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"plate L={args.L}, clamped left, top traction (E, nu, amp, angle) seed 2",
-                       "L": args.L, "dofs": 2 * 4 ** args.L, "batch": 1, "accept_rel_residual": args.tol},
+            "config": {"workload": f"plate L={args.L} ({2 * 4 ** args.L} DOFs), clamped left, constant top-edge "
+                                   f"traction; (E, nu, amp, angle) from the held-out seed-2 set",
+                       "L": args.L, "batch": 1, "accept_rel_residual": args.tol},
             "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cpu_threads(), "kind": "oracle",
                              "sample": desc, "cpu": cpu_model()},
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -255,17 +279,21 @@ def main():
     args = parse()
     if args.impl == "reference":
         return reference_main(args)
+    import ctypes as C
+
+    import numpy as np
     import torch
+
     import __graft_entry__
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
     if world > 1:
         import torch.distributed as dist
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     else:
-        dist = None
         torch.cuda.set_device(0)
     __graft_entry__.build()
     import paper_2501_07778_gb300 as q
@@ -276,22 +304,28 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    batch = args.batch or (4 if args.form == "fast" else 1)
     nsteps = args.warmup + args.steps
-    probs = problems(args.L, nsteps * args.batch, rank, world)
+    P, probs = workload(args.L, nsteps * batch, rank, world)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > 129 MB L2
 
-    # warm-up
+    # one-time precompute (untimed): the warm-start network
+    net, ws_info = None, None
+    if args.form == "fast":
+        net, ws_info = train_warm_start(args.L, args.tol, args.train_steps)
+
+    def step_slice(st):
+        return P[st * batch:(st + 1) * batch], probs[st * batch:(st + 1) * batch]
+
     for st in range(args.warmup):
-        for b in range(args.batch):
-            run_problem(probs[st * args.batch + b], args.form, args.tol)
+        run_step(args.form, *step_slice(st), net, args.tol, args.workers)
     barrier()
 
     sampler = ClockSampler(local)
     sampler.start()
     launches0 = lib.qtt_kernel_launches()
-    accepted = 0
-    total = 0
+    accepted = total = 0
     ms = 0.0
     infos = []
     barrier()
@@ -300,14 +334,14 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for b in range(args.batch):
-            u, info = run_problem(probs[st * args.batch + b], args.form, args.tol)
-            total += 1
-            accepted += int(info["rel_residual"] <= args.tol)
-            infos.append(info)
+        us, inf = run_step(args.form, *step_slice(st), net, args.tol, args.workers)
         e1.record(stream)
         e1.synchronize()
         ms += e0.elapsed_time(e1)
+        for i in inf:
+            total += 1
+            accepted += int(0 < i["rel_residual"] <= args.tol)
+            infos.append(i)
     barrier()
     launches = lib.qtt_kernel_launches() - launches0
     clocks = sampler.stop()
@@ -320,61 +354,59 @@ def main():
     ms_all, acc_all, tot_all = float(t[0]), float(t[1]), float(t[2])
     value = acc_all / (ms_all / 1e3) if ms_all > 0 else 0.0
 
-    # ---- dominant kernel: one extra profiled step (CUDA events per launch)
+    # ---- dominant kernel class: one extra step with CUDA events per launch
     lib.qtt_profile_enable(1)
-    run_problem(probs[-1], args.form, args.tol)
+    run_step(args.form, *step_slice(nsteps - 1), net, args.tol, args.workers)
     torch.cuda.synchronize()
     lib.qtt_profile_enable(0)
-    import ctypes as C
     classes = {0: "gemm_f64", 1: "gemm_f32", 2: "core_product", 3: "qr_panel", 4: "jacobi_svd", 5: "lu_panel",
                6: "permute"}
     prof = {}
     for cid, nm in classes.items():
         a, f_, b_, n_ = C.c_double(), C.c_double(), C.c_double(), C.c_longlong()
         lib.qtt_profile_read(cid, C.byref(a), C.byref(f_), C.byref(b_), C.byref(n_))
-        prof[nm] = {"ms": a.value, "flops": f_.value, "bytes": b_.value, "launches": n_.value}
+        prof[nm] = {"ms": round(a.value, 3), "gflop": round(f_.value / 1e9, 3), "gbytes": round(b_.value / 1e9, 3),
+                    "launches": n_.value}
     dom = max(prof, key=lambda k: prof[k]["ms"])
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    hbm = peaks.get("hbm_gbs", 6800.0)
     d = prof[dom]
+    sec = d["ms"] / 1e3
     if dom in ("gemm_f64", "qr_panel", "jacobi_svd", "lu_panel"):
-        bound, peak, unit = "alu", 1.25, "TFLOP/s"     # FP64 DFMA rate of the GPU
-        achieved = d["flops"] / (d["ms"] / 1e3) / 1e12 if d["ms"] > 0 else 0.0
+        bound, peak, unit, src = "alu", 1.25, "TFLOP/s", "FP64 rate of GB300 (2 DFMA/SM/clk x 152 SMs x 2.07 GHz)"
+        achieved = d["gflop"] / 1e3 / sec if sec > 0 else 0.0
     elif dom == "gemm_f32":
         bound, peak, unit = "alu", 152 * 128 * 2 * 2.07e9 / 1e12, "TFLOP/s"
-        achieved = d["flops"] / (d["ms"] / 1e3) / 1e12 if d["ms"] > 0 else 0.0
+        src = "FP32 SIMT: 152 SMs x 128 lanes x 2 flops x 2.07 GHz"
+        achieved = d["gflop"] / 1e3 / sec if sec > 0 else 0.0
     else:
-        bound, peak, unit = "hbm", hbm, "GB/s"
-        achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9 if d["ms"] > 0 else 0.0
-    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak if peak else None, "traffic": None,
-                "launches_in_profiled_step": d["launches"], "avg_launch_us": 1e3 * d["ms"] / max(1, d["launches"]),
-                "peak_source": "FP64: GB300 rate 1.25 TFLOP/s; FP32: 152 SMs x 128 lanes x 2 x 2.07 GHz; "
-                               "HBM: MEASURED_PEAKS.json",
-                "classes": prof}
+        bound, peak, unit, src = "hbm", peaks.get("hbm_gbs", 6800.0), "GB/s", "MEASURED_PEAKS.json hbm_gbs"
+        achieved = d["gbytes"] / sec if sec > 0 else 0.0
+    roofline = {"bound": bound, "kernel": dom, "achieved": round(achieved, 4), "peak": round(peak, 2), "unit": unit,
+                "frac": round(achieved / peak, 5) if peak else None, "traffic": None,
+                "launches_in_profiled_step": d["launches"],
+                "avg_launch_us": round(1e3 * d["ms"] / max(1, d["launches"]), 2),
+                "peak_source": src, "classes": prof,
+                "note": "event-timed over one extra step of the same workload (events bracket every launch)"}
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the public API, host buffers in and out
     e2e = None
     if not args.no_e2e:
-        import numpy as np
         h2d = d2h = 0
-        t0 = time.perf_counter()
-        n_e2e = 0
         acc_e2e = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         for st in range(args.warmup, nsteps):
-            for b in range(args.batch):
-                prob = probs[st * args.batch + b]
-                st_ = q.make_problem_struct(prob)
-                h2d += 8 * 2 * len(prob.patches) + 4 * 4 * len(prob.bc) + 48 * len(prob.traction) + 64
-                u, info = run_problem(prob, args.form, args.tol)
-                cores = u.cores()                      # device -> host read of the result
+            par, pr = step_slice(st)
+            h2d += par.nbytes + sum(8 * 2 + 4 * 4 + 24 for _ in pr)     # params / struct arrays per problem
+            us, inf = run_step(args.form, par, pr, net, args.tol, args.workers)
+            for u, i in zip(us, inf):
+                cores = u.cores()                                         # device -> host read of the result
                 d2h += sum(c.nbytes for c in cores)
-                n_e2e += 1
-                acc_e2e += int(info["rel_residual"] <= args.tol)
+                acc_e2e += int(0 < i["rel_residual"] <= args.tol)
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
         e2e = {"value": acc_e2e / te if te > 0 else 0.0, "unit": "solves/s",
@@ -388,7 +420,7 @@ def main():
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         gs = int(statistics.median([i["sweeps"] for i in infos])) if infos else None
-        per, desc = oracle_sample(probs[args.warmup], args.tol, args.cpu_budget, gpu_sweeps=gs)
+        per, desc = oracle_sample(probs[args.warmup], args.tol, args.cpu_budget, sweeps_needed=gs)
         cpu = {"value": 1.0 / per, "unit": "solves/s", "cores": cpu_threads(), "kind": "oracle", "sample": desc,
                "cpu": cpu_model()}
 
@@ -398,13 +430,14 @@ def main():
             "data": "synthetic",
             "config": {"workload": f"plate L={args.L} ({2 * 4 ** args.L} DOFs), clamped left, constant top-edge "
                                    f"traction; (E, nu, amp, angle) from the held-out seed-2 set",
-                       "form": args.form, "L": args.L, "batch_per_rank": args.batch,
+                       "form": args.form, "L": args.L, "batch_per_rank": batch, "workers": args.workers,
                        "accept_rel_residual": args.tol, "l2": "flushed (256 MB write) before every timed step"},
             "accepted": int(acc_all), "solved": int(tot_all),
             "solve_stats": {"sweeps": [i["sweeps"] for i in infos], "max_rank": [i["max_rank"] for i in infos],
                             "rel_residual": [i["rel_residual"] for i in infos],
-                            "refinements": [i["refinements"] for i in infos]},
-            "gpu_launches": int(launches), "clocks": clocks, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e}
+                            "local_iters": [i["local_iters"] for i in infos]},
+            "warm_start": ws_info, "gpu_launches": int(launches), "clocks": clocks, "roofline": roofline,
+            "cpu_baseline": cpu, "e2e": e2e}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -221,11 +221,67 @@ int qtt_solve(const qtt_tensor* K, const qtt_tensor* f, const qtt_tensor* x0,
               const qtt_tensor* z0, const qtt_solve_opts* opts, qtt_tensor** x,
               qtt_solve_info* info, void* stream);
 
+/* Batched solves of count independent problems (uneven levels, patch counts
+ * and ranks are fine): K[i] u[i] = f[i] with optional initial guesses x0[i]
+ * (x0 NULL or entries NULL = cold start), one options struct for all.  A
+ * work queue is drained by nworkers host threads (<= 0: 8), each issuing its
+ * solve's kernels on its own stream; `stream` waits for all of them.  Creates
+ * x[i]; info (may be NULL) receives one record per problem.  Returns the
+ * first error met (the other results stay valid), else QTT_OK; per-problem
+ * convergence is in info[i].status. */
+int qtt_solve_batched(int count, const qtt_tensor* const* K, const qtt_tensor* const* f,
+                      const qtt_tensor* const* x0, const qtt_solve_opts* opts, int nworkers,
+                      qtt_tensor** x, qtt_solve_info* info, void* stream);
+
 /* FP64 relative residual ||f - K u|| / ||f||: the product K u and the sum are
  * formed in QTT and normed by orthogonalisation (no rounding).  Writes *out
  * on the host; synchronises the stream. */
 int qtt_residual(const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* f,
                  double* out, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Learned warm start (growth pattern of this engine; not in the paper)      */
+/* ------------------------------------------------------------------------ */
+/* A 3-layer MLP maps nin load/material features to the cores of a rank-r QTT
+ * that seeds qtt_solve.  All arrays are DEVICE float32, column-major, with
+ * the batch as the slowest index: phi (nin x B), h1, h2 (H x B), out (P x B),
+ * W1 (H x nin), W2 (H x H), W3 (P x H), biases of the layer widths.
+ *   h1 = tanh(W1 phi + b1), h2 = tanh(W2 h1 + b2), out = W3 h2 + b3.
+ * Core k of sample b is the next r_{k-1} n_k r_k entries of out[:, b]
+ * (column-major (r_{k-1}, n_k, r_k), r_0 = r_d = 1). */
+int qtt_ws_forward(int B, int nin, int H, int P, const float* W1, const float* b1, const float* W2,
+                   const float* b2, const float* W3, const float* b3, const float* phi,
+                   float* h1, float* h2, float* out, void* stream);
+
+/* Gradients of the MLP parameters given dLoss/dout (P x B); work is device
+ * scratch of 2 H B floats owned by the caller. */
+int qtt_ws_backward(int B, int nin, int H, int P, const float* W2, const float* W3, const float* phi,
+                    const float* h1, const float* h2, const float* gout, float* gW1, float* gb1,
+                    float* gW2, float* gb2, float* gW3, float* gb3, float* work, void* stream);
+
+/* Host Gram matrix gram[t nbasis + u] = <basis_t, basis_u> of FP32 basis
+ * tensors (TT inner products; synchronises the stream). */
+int qtt_ws_basis_gram(int d, int nbasis, const qtt_tensor* const* basis, double* gram, void* stream);
+
+/* Gauge-invariant loss of each sample, loss[b] = ||X_hat_b - X_b||^2 /
+ * ||X_b||^2, with X_hat_b the predicted TT and the target
+ * X_b = sum_t coef[b nbasis + t] basis[t] (host coef; FP32 basis tensors of
+ * the same modes), computed from TT inner products (transfer matrices).
+ * gram: host Gram matrix of the basis from qtt_ws_basis_gram, or NULL to
+ * compute it here.  Writes loss (device, B) and gout = d(mean loss)/d(out)
+ * (device, P x B). */
+int qtt_ws_tt_loss(int B, int d, const int* modes, int r, const float* out, int nbasis,
+                   const qtt_tensor* const* basis, const double* coef, const double* gram, float* loss,
+                   float* gout, void* stream);
+
+/* One Adam step on n parameters (device arrays; t >= 1 is the step number). */
+int qtt_ws_adam(int n, float* w, const float* g, float* m, float* v, float lr, float b1, float b2,
+                float eps, int t, void* stream);
+
+/* New FP64 qtt_tensor from one predicted output column (device), the first
+ * core multiplied by scale. */
+int qtt_ws_to_tensor(const float* out_row, int d, const int* modes, int r, double scale,
+                     qtt_tensor** x, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Diagnostics (not part of the method)                                      */

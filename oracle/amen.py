@@ -119,8 +119,9 @@ def _orth_right(cores: Cores) -> Cores:
 def amen_solve(A: Cores, y: Cores, x0: Cores, z0: Cores, eps: float,
                max_sweeps: int = 20, max_rank: int = 1 << 30,
                local_direct_max: int = 2500, gmres_restart: int = 40,
-               gmres_maxiter: int = 4, verbose: bool = False):
-    """Solve A x = y; returns (x cores, AmenInfo)."""
+               gmres_maxiter: int = 4, verbose: bool = False, on_sweep=None):
+    """Solve A x = y; returns (x cores, AmenInfo).  on_sweep(sweep, max_res),
+    if given, is called after every sweep (timing instrumentation only)."""
     D = len(A)
     x = [c.copy() for c in x0]
     z = [c.copy() for c in z0]
@@ -218,6 +219,8 @@ def amen_solve(A: Cores, y: Cores, x0: Cores, z0: Cores, eps: float,
             ZY_L = _left_XY(ZY_L, z[k], y[k])
         info.sweeps = sweep + 1
         info.max_res_history.append(max_res)
+        if on_sweep is not None:
+            on_sweep(sweep + 1, max_res)
         if verbose:
             print(f"sweep {sweep + 1}: max local res {max_res:.3e} ranks {tt.ranks(x)}")
         if max_res <= eps:

@@ -210,6 +210,25 @@ def solve_opts(tol=1e-8, max_rank=0, kick_rank=0, max_sweeps=0, local_direct_max
                         precision, refine_max, inner_tol, verbose)
 
 
+def qtt_solve_batched(Ks: List[QTT], fs: List[QTT], x0s: Optional[List[Optional[QTT]]] = None, nworkers: int = 0,
+                      stream=None, **opts):
+    """Solve independent problems together; returns (list of u, list of info dicts)."""
+    n = len(Ks)
+    o = solve_opts(**opts)
+    Karr = (C.c_void_p * n)(*[k.handle for k in Ks])
+    farr = (C.c_void_p * n)(*[f.handle for f in fs])
+    xarr = None
+    if x0s is not None:
+        xarr = (C.c_void_p * n)(*[(x.handle if x is not None else None) for x in x0s])
+    out = (C.c_void_p * n)()
+    infos = (QttSolveInfo * n)()
+    rc = lib().qtt_solve_batched(n, Karr, farr, xarr, C.byref(o), nworkers, out, infos, _stream(stream))
+    _check(rc, "qtt_solve_batched", ok=(0, _lib.QTT_ENOCONV))
+    us = [QTT(C.c_void_p(out[i])) if out[i] else None for i in range(n)]
+    ds = [{k: getattr(infos[i], k) for k, _ in QttSolveInfo._fields_} for i in range(n)]
+    return us, ds
+
+
 def qtt_solve(K: QTT, f: QTT, x0: Optional[QTT] = None, z0: Optional[QTT] = None, stream=None, check=True,
               **opts):
     """Solve K u = f by AMEn; returns (u, info dict)."""

@@ -62,6 +62,15 @@ SIGNATURES = {
     "qtt_to_full": (C.c_int, [P, P, C.c_size_t, C.c_int, P]),
     "qtt_solve": (C.c_int, [P, P, P, P, C.POINTER(QttSolveOpts), PP, C.POINTER(QttSolveInfo), P]),
     "qtt_residual": (C.c_int, [P, P, P, C.POINTER(C.c_double), P]),
+    "qtt_solve_batched": (C.c_int, [C.c_int, PP, PP, PP, C.POINTER(QttSolveOpts), C.c_int, PP,
+                                    C.POINTER(QttSolveInfo), P]),
+    "qtt_ws_forward": (C.c_int, [C.c_int] * 4 + [P] * 10 + [P]),
+    "qtt_ws_backward": (C.c_int, [C.c_int] * 4 + [P] * 13 + [P]),
+    "qtt_ws_basis_gram": (C.c_int, [C.c_int, C.c_int, PP, C.POINTER(C.c_double), P]),
+    "qtt_ws_tt_loss": (C.c_int, [C.c_int, C.c_int, IP, C.c_int, P, C.c_int, PP, C.POINTER(C.c_double),
+                                 C.POINTER(C.c_double), P, P, P]),
+    "qtt_ws_adam": (C.c_int, [C.c_int, P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int, P]),
+    "qtt_ws_to_tensor": (C.c_int, [P, C.c_int, IP, C.c_int, C.c_double, PP, P]),
     "qtt_kernel_launches": (C.c_ulonglong, []),
     "qtt_profile_enable": (C.c_int, [C.c_int]),
     "qtt_profile_read": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),

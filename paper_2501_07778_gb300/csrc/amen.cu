@@ -25,6 +25,7 @@
 #include "tt_ops.cuh"
 
 namespace qtt {
+double residual64(cudaStream_t s, const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* f);
 namespace {
 
 using Tptr = std::unique_ptr<qtt_tensor, void (*)(qtt_tensor*)>;
@@ -145,6 +146,26 @@ __global__ void scale_rows_kernel(int rows, int cols, const T* A, int lda, const
   }
 }
 
+// CG step with device scalars: alpha = rr / (p.Bp); d += alpha p; r -= alpha Bp
+template <typename U>
+__global__ void cg_step_kernel(U* d, U* r, const U* p, const U* q, const double* rr, const double* pq, int n) {
+  const double den = *pq;
+  const double alpha = den > 0.0 ? *rr / den : 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    d[i] = (U)((double)d[i] + alpha * (double)p[i]);
+    r[i] = (U)((double)r[i] - alpha * (double)q[i]);
+  }
+}
+
+// p = r + (rr_new / rr_old) p
+template <typename U>
+__global__ void cg_dir_kernel(U* p, const U* r, const double* rr_new, const double* rr_old, int n) {
+  const double old = *rr_old;
+  const double beta = old > 0.0 ? *rr_new / old : 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    p[i] = (U)((double)r[i] + beta * (double)p[i]);
+}
+
 // deterministic residual proxy when none is given: smooth sign-varying values
 template <typename T>
 __global__ void proxy_kernel(T* c, long long n, int k) {
@@ -182,6 +203,7 @@ struct Amen {
   double tol;
   int max_rank, kick, max_sweeps, ndir, restart, cycles, verbose;
   bool mixed_local = false;   // FP32 operator inside the local GMRES cycles
+  double global_check = 0.0;  // > 0: check the FP64 global residual once max local <= global_check * tol
   // interfaces: PhiR[k] (bond k), k = 0..D
   std::vector<DBuf<T>> XAX_R, XY_R, ZAX_R, ZY_R;
   DBuf<T> XAX_L, XY_L, ZAX_L, ZY_L, XAX_Ln, XY_Ln, ZAX_Ln, ZY_Ln;
@@ -378,6 +400,73 @@ struct Amen {
     return rel;
   }
 
+  // Conjugate gradients for a symmetric positive definite local operator,
+  // in cycles of `restart` iterations: each cycle recomputes the residual in
+  // T, runs CG on B d = g - B x with the operator in U (FP32 when mixed) and
+  // adds d to x in T.  All CG scalars stay on the device within a cycle.
+  template <typename U>
+  double cg(int k, const T* PhiL, int r0, const T* PhiR, int r1, const T* g, double gn, T* xk, double rtol) {
+    const int n = A->n[k], R0 = rA(k), R1 = rA(k + 1);
+    const int N = r0 * n * r1;
+    const int m = std::max(1, restart);
+    Arena sc(s);
+    const U* PL = reinterpret_cast<const U*>(PhiL);
+    const U* PR = reinterpret_cast<const U*>(PhiR);
+    const U* Ak = reinterpret_cast<const U*>(A->core[k]);
+    if (sizeof(U) != sizeof(T)) {
+      U* a = sc.alloc<U>((size_t)r0 * R0 * r0);
+      convert<T, U>(s, PhiL, a, (size_t)r0 * R0 * r0);
+      U* b = sc.alloc<U>((size_t)r1 * R1 * r1);
+      convert<T, U>(s, PhiR, b, (size_t)r1 * R1 * r1);
+      U* c = sc.alloc<U>((size_t)R0 * n * n * R1);
+      convert<T, U>(s, (const T*)A->core[k], c, (size_t)R0 * n * n * R1);
+      PL = a;
+      PR = b;
+      Ak = c;
+    }
+    U* d = sc.alloc<U>(N);
+    U* r = sc.alloc<U>(N);
+    U* p = sc.alloc<U>(N);
+    U* qv = sc.alloc<U>(N);
+    T* wT = sc.alloc<T>(N);
+    double* sc4 = sc.alloc<double>(3);       // rr_old, rr_new, pq
+    double rel = 1.0;
+    for (int cyc = 0; cyc < cycles; ++cyc) {
+      Arena it(s);
+      local_apply(PhiL, r0, r0, k, PhiR, r1, r1, xk, wT, it);
+      axpby<T>(s, N, T(1), g, T(-1), wT);     // residual in T
+      double beta = host_norm(wT, N);
+      rel = gn > 0 ? beta / gn : beta;
+      if (rel <= rtol || beta == 0.0) break;
+      convert<T, U>(s, wT, r, N);
+      QTT_CUDA(cudaMemcpyAsync(p, r, sizeof(U) * N, cudaMemcpyDeviceToDevice, s));
+      QTT_CUDA(cudaMemsetAsync(d, 0, sizeof(U) * N, s));
+      double* rr_old = sc4;
+      double* rr_new = sc4 + 1;
+      double* pq = sc4 + 2;
+      dotp<U>(s, r, r, N, rr_old);
+      for (int j = 0; j < m; ++j) {
+        Arena ij(s);
+        apply_local<U>(s, ij, PL, r0, r0, Ak, R0, n, R1, PR, r1, r1, p, qv);
+        dotp<U>(s, p, qv, N, pq);
+        cg_step_kernel<U><<<grid_for(N), 256, 0, s>>>(d, r, p, qv, rr_old, pq, N);
+        QTT_CHECK_LAUNCH();
+        dotp<U>(s, r, r, N, rr_new);
+        cg_dir_kernel<U><<<grid_for(N), 256, 0, s>>>(p, r, rr_new, rr_old, N);
+        QTT_CHECK_LAUNCH();
+        std::swap(rr_old, rr_new);
+      }
+      if (sizeof(U) != sizeof(T)) {
+        convert<U, T>(s, d, wT, N);
+        axpby<T>(s, N, T(1), wT, T(1), xk);
+      } else {
+        axpby<T>(s, N, T(1), reinterpret_cast<const T*>(d), T(1), xk);
+      }
+      if (info) info->local_iters += m;
+    }
+    return rel;
+  }
+
   double local_residual(int k, const T* PhiL, int r0, const T* PhiR, int r1, const T* g, double gn, const T* xk) {
     const int N = r0 * A->n[k] * r1;
     Arena sc(s);
@@ -431,7 +520,10 @@ struct Amen {
           lu_solve<T>(s, sc, N, Bm, N, sol, N, 1, dinfo);
         } else {
           QTT_CUDA(cudaMemcpyAsync(sol, xk, sizeof(T) * N, cudaMemcpyDeviceToDevice, s));
-          if (mixed_local && sizeof(T) == 8) gmres<float>(k, XAX_L.p, r0, PhiR, r1, g, gn, sol, delta);
+          if (A->sym) {
+            if (mixed_local && sizeof(T) == 8) cg<float>(k, XAX_L.p, r0, PhiR, r1, g, gn, sol, delta);
+            else cg<T>(k, XAX_L.p, r0, PhiR, r1, g, gn, sol, delta);
+          } else if (mixed_local && sizeof(T) == 8) gmres<float>(k, XAX_L.p, r0, PhiR, r1, g, gn, sol, delta);
           else gmres<T>(k, XAX_L.p, r0, PhiR, r1, g, gn, sol, delta);
         }
         if (info) info->local_solves += 1;
@@ -540,6 +632,19 @@ struct Amen {
         status = QTT_OK;
         break;
       }
+      // Near the tolerance the local residuals can hover above it while the
+      // global one is already below (the local ones are projections of the
+      // last iterate's residual, measured before each core's update): once
+      // they are within global_check x tol, the FP64 global residual decides.
+      if (sizeof(T) == 8 && global_check > 0 && max_res <= global_check * tol) {
+        const double rel = residual64(s, A, x, y);
+        if (info) info->rel_residual = rel;
+        if (verbose) fprintf(stderr, "[qtt_solve f64] sweep %d global FP64 rel residual %.3e\n", sweep + 1, rel);
+        if (rel <= tol) {
+          status = QTT_OK;
+          break;
+        }
+      }
     }
     return status;
   }
@@ -589,10 +694,11 @@ int amen_run(cudaStream_t s, const qtt_tensor* K, const qtt_tensor* f, qtt_tenso
   am.max_sweeps = o.max_sweeps > 0 ? o.max_sweeps : 30;
   am.ndir = o.local_direct_max > 0 ? o.local_direct_max : 2048;
   am.restart = std::min(o.local_restart > 0 ? o.local_restart : 40, 64);
-  am.cycles = o.local_max_cycles > 0 ? o.local_max_cycles : 8;
+  am.cycles = o.local_max_cycles > 0 ? o.local_max_cycles : 20;
   am.verbose = o.verbose;
   am.info = info;
   am.mixed_local = mixed_local;
+  am.global_check = 30.0;
   am.dscal = ar.alloc<double>(4);
   int rc = am.run();
   QTT_CUDA(cudaStreamSynchronize(s));
@@ -612,10 +718,34 @@ double erank_of(const qtt_tensor* x) {
 
 }  // namespace
 
+// FP64 relative residual ||f - K u|| / ||f||.  The product K u is formed
+// exactly by the QTT matvec in FP64 (ranks R r).  When the full vector fits
+// (<= 2^28 entries) the norm is taken after expanding f - K u to full format
+// (one FP64 GEMM of the left and right partial expansions: O(N R r) flops,
+// exact up to rounding); otherwise the sum is normed by FP64 left
+// orthogonalisation (O(D (R r)^3) flops).
 double residual64(cudaStream_t s, const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* f) {
   Arena ar(s);
   auto Ku = own(product<double>(s, K, u));
   auto r = own(tt_sum<double>(s, 1.0, f, -1.0, Ku.get()));
+  long long total = 1;
+  for (int k = 0; k < r->d; ++k) total *= r->n[k];
+  if (total <= (1LL << 28)) {
+    double* full = ar.alloc<double>(total);
+    to_full<double>(s, ar, r.get(), full, (size_t)total, QTT_ORDER_Z_BLOCK);
+    double* dv = ar.alloc<double>(1);
+    sumsq<double>(s, full, (size_t)total, dv);
+    double rn2 = 0;
+    QTT_CUDA(cudaMemcpyAsync(&rn2, dv, sizeof(double), cudaMemcpyDeviceToHost, s));
+    double* ff = ar.alloc<double>(total);
+    to_full<double>(s, ar, f, ff, (size_t)total, QTT_ORDER_Z_BLOCK);
+    double* df = ar.alloc<double>(1);
+    sumsq<double>(s, ff, (size_t)total, df);
+    double fn2 = 0;
+    QTT_CUDA(cudaMemcpyAsync(&fn2, df, sizeof(double), cudaMemcpyDeviceToHost, s));
+    QTT_CUDA(cudaStreamSynchronize(s));
+    return fn2 > 0 ? std::sqrt(rn2 / fn2) : std::sqrt(rn2);
+  }
   double rn = norm<double>(s, ar, r.get());
   double fn = norm<double>(s, ar, f);
   return fn > 0 ? rn / fn : rn;
@@ -632,7 +762,7 @@ int solve(const qtt_tensor* K, const qtt_tensor* f, const qtt_tensor* x0, const 
   qtt_solve_info local{};
   qtt_solve_info* inf = info ? info : &local;
   std::memset(inf, 0, sizeof(*inf));
-  const int rho = o.kick_rank > 0 ? o.kick_rank : 4;
+  const int rho = o.kick_rank > 0 ? o.kick_rank : 8;
   int rc = QTT_OK;
   if (o.precision == QTT_F64 || o.precision == QTT_F32) {
     const int prec = o.precision;
@@ -647,7 +777,9 @@ int solve(const qtt_tensor* K, const qtt_tensor* f, const qtt_tensor* x0, const 
     rc = prec == QTT_F64 ? amen_run<double>(s, Ku, fu, x.get(), z.get(), o.tol, o, inf)
                          : amen_run<float>(s, Ku, fu, x.get(), z.get(), o.tol, o, inf);
     if (prec == QTT_F64) {
-      inf->rel_residual = residual64(s, K, x.get(), f);
+      // a passing in-sweep check stops the sweeps at once, so a stored value
+      // <= tol is the final iterate's residual; otherwise measure it now
+      if (!(inf->rel_residual > 0 && inf->rel_residual <= o.tol)) inf->rel_residual = residual64(s, K, x.get(), f);
     }
     *xout = x.release();
   } else {
@@ -663,31 +795,22 @@ int solve(const qtt_tensor* K, const qtt_tensor* f, const qtt_tensor* x0, const 
     Tptr u = x0 ? own(tensor_clone(x0, QTT_F64, s)) : default_x0(s, f, QTT_F64);
     Tptr z = z0 ? own(tensor_clone(z0, QTT_F64, s)) : default_z0(s, f, rho, QTT_F64);
     rc = amen_run<double>(s, K, f, u.get(), z.get(), o.tol, o, inf, true);
-    const double fn = [&] {
-      Arena ar(s);
-      return norm<double>(s, ar, f);
-    }();
     for (int it = 0;; ++it) {
       Tptr r = own(nullptr);
-      double rel = 1.0;
+      const double rel = (it == 0 && inf->rel_residual > 0 && inf->rel_residual <= o.tol)
+                             ? inf->rel_residual
+                             : residual64(s, K, u.get(), f);
+      inf->rel_residual = rel;
+      if (o.verbose) fprintf(stderr, "[qtt_solve mixed] check %d: FP64 rel residual %.3e\n", it, rel);
+      if (rel <= o.tol || it >= refine_max) {
+        rc = rel <= o.tol ? QTT_OK : QTT_ENOCONV;
+        break;
+      }
       {
+        // r = f - K u by the FP64 QTT matvec, rounded in FP64
         Arena ar(s);
         auto Ku = own(product<double>(s, K, u.get()));
         r = own(tt_sum<double>(s, 1.0, f, -1.0, Ku.get()));
-        left_orthogonalize<double>(s, ar, r.get(), r->d - 1);
-        double* dv = ar.alloc<double>(1);
-        sumsq<double>(s, (const double*)r->core[r->d - 1], core_elems(r.get(), r->d - 1), dv);
-        double rn2 = 0;
-        QTT_CUDA(cudaMemcpyAsync(&rn2, dv, sizeof(double), cudaMemcpyDeviceToHost, s));
-        QTT_CUDA(cudaStreamSynchronize(s));
-        rel = std::sqrt(rn2) / (fn > 0 ? fn : 1.0);
-        inf->rel_residual = rel;
-        if (o.verbose) fprintf(stderr, "[qtt_solve mixed] check %d: FP64 rel residual %.3e\n", it, rel);
-        if (rel <= o.tol || it >= refine_max) {
-          rc = rel <= o.tol ? QTT_OK : QTT_ENOCONV;
-          break;
-        }
-        // the sweep above left r's cores left-orthogonal: round them in FP64
         round_tt<double>(s, ar, r.get(), std::min(1e-2, inner), 0);
       }
       auto d = default_x0(s, f, QTT_F64);
@@ -713,6 +836,7 @@ int solve(const qtt_tensor* K, const qtt_tensor* f, const qtt_tensor* x0, const 
 extern "C" int qtt_solve(const qtt_tensor* K, const qtt_tensor* f, const qtt_tensor* x0, const qtt_tensor* z0,
                          const qtt_solve_opts* opts, qtt_tensor** x, qtt_solve_info* info, void* stream) {
   try {
+    qtt::StreamScope scope_(reinterpret_cast<cudaStream_t>(stream));
     int rc = qtt::solve(K, f, x0, z0, opts, x, info, reinterpret_cast<cudaStream_t>(stream));
     if (rc == QTT_ENOCONV) qtt::set_last_error("qtt_solve: tolerance not reached");
     return rc;

@@ -557,6 +557,9 @@ void assemble(const qtt_problem* P, qtt_tensor** Kout, qtt_tensor** fout, cudaSt
   round_tt<double>(s, ar, K.get(), tol, 0);
   round_tt<double>(s, ar, f.get(), tol, 0);
   QTT_CUDA(cudaStreamSynchronize(s));
+  // one patch: K = M K0 M + (I - M) with K0 symmetric is symmetric; the
+  // concatenated multi-patch system is not (Section 3.6 reading)
+  K->sym = (q == 1) ? 1 : 0;
   *Kout = K.release();
   *fout = f.release();
 }
@@ -565,6 +568,7 @@ void assemble(const qtt_problem* P, qtt_tensor** Kout, qtt_tensor** fout, cudaSt
 
 extern "C" int qtt_assemble_stiffness(const qtt_problem* p, qtt_tensor** K, qtt_tensor** f, void* stream) {
   try {
+    qtt::StreamScope scope_(reinterpret_cast<cudaStream_t>(stream));
     qtt::assemble(p, K, f, reinterpret_cast<cudaStream_t>(stream));
     return QTT_OK;
   } catch (const qtt::QttError& e) {

@@ -1,0 +1,97 @@
+// qtt_solve_batched: many independent solves (uneven levels, patch counts
+// and ranks) drained from one work queue by worker threads, each issuing its
+// solve's kernels on its own non-blocking stream.  One AMEn step is a chain
+// of small dependent contractions that cannot fill 152 SMs, so concurrent
+// solves are what keeps the GPU busy; the caller's stream waits on every
+// worker stream before the call returns its results.
+#include <atomic>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+
+namespace qtt {
+int solve(const qtt_tensor* K, const qtt_tensor* f, const qtt_tensor* x0, const qtt_tensor* z0,
+          const qtt_solve_opts* opts, qtt_tensor** xout, qtt_solve_info* info, cudaStream_t s);
+}
+
+using namespace qtt;
+
+extern "C" int qtt_solve_batched(int count, const qtt_tensor* const* K, const qtt_tensor* const* f,
+                                 const qtt_tensor* const* x0, const qtt_solve_opts* opts, int nworkers,
+                                 qtt_tensor** x, qtt_solve_info* info, void* stream) {
+  try {
+    QTT_REQUIRE(count >= 0 && K && f && opts && x, "qtt_solve_batched: null argument");
+    if (count == 0) return QTT_OK;
+    int dev = 0;
+    QTT_CUDA(cudaGetDevice(&dev));
+    const int W = std::max(1, std::min(nworkers > 0 ? nworkers : 8, count));
+    cudaStream_t caller = reinterpret_cast<cudaStream_t>(stream);
+    // inputs may still be in flight on the caller's stream
+    cudaEvent_t ready;
+    QTT_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    QTT_CUDA(cudaEventRecord(ready, caller));
+    std::vector<cudaStream_t> streams(W);
+    for (int w = 0; w < W; ++w) {
+      QTT_CUDA(cudaStreamCreateWithFlags(&streams[w], cudaStreamNonBlocking));
+      QTT_CUDA(cudaStreamWaitEvent(streams[w], ready, 0));
+    }
+    std::atomic<int> next{0};
+    std::atomic<int> first_error{QTT_OK};
+    std::mutex msg_mu;
+    std::string first_msg;
+    for (int i = 0; i < count; ++i) x[i] = nullptr;
+    auto worker = [&](int w) {
+      cudaSetDevice(dev);
+      StreamScope scope_(streams[w]);
+      for (;;) {
+        const int i = next.fetch_add(1);
+        if (i >= count) break;
+        qtt_solve_info local{};
+        qtt_solve_info* inf = info ? &info[i] : &local;
+        try {
+          int rc = solve(K[i], f[i], x0 ? x0[i] : nullptr, nullptr, opts, &x[i], inf, streams[w]);
+          inf->status = rc;
+        } catch (const QttError& e) {
+          inf->status = e.code;
+          int z = QTT_OK;
+          if (first_error.compare_exchange_strong(z, e.code)) {
+            std::lock_guard<std::mutex> lk(msg_mu);
+            first_msg = e.what();
+          }
+        } catch (const std::exception& e) {
+          inf->status = QTT_EINVAL;
+          int z = QTT_OK;
+          if (first_error.compare_exchange_strong(z, QTT_EINVAL)) {
+            std::lock_guard<std::mutex> lk(msg_mu);
+            first_msg = e.what();
+          }
+        }
+      }
+    };
+    std::vector<std::thread> threads;
+    for (int w = 0; w < W; ++w) threads.emplace_back(worker, w);
+    for (auto& t : threads) t.join();
+    for (int w = 0; w < W; ++w) {
+      cudaEvent_t done;
+      QTT_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+      QTT_CUDA(cudaEventRecord(done, streams[w]));
+      QTT_CUDA(cudaStreamWaitEvent(caller, done, 0));
+      cudaEventDestroy(done);
+      cudaStreamDestroy(streams[w]);
+    }
+    cudaEventDestroy(ready);
+    // results now belong to the caller's stream (the worker streams are gone)
+    for (int i = 0; i < count; ++i)
+      if (x[i]) x[i]->stream = caller;
+    if (first_error.load() != QTT_OK) {
+      set_last_error("qtt_solve_batched: " + first_msg);
+      return first_error.load();
+    }
+    return QTT_OK;
+  } catch (const QttError& e) {
+    set_last_error(e.what());
+    return e.code;
+  }
+}

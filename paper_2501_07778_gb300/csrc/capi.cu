@@ -97,6 +97,7 @@ int qtt_tensor_core_ptr(const qtt_tensor* t, int k, void** dev_ptr) {
 int qtt_tensor_copy(const qtt_tensor* src, int prec, qtt_tensor** out, void* stream) {
   QTT_API_BEGIN
   QTT_REQUIRE(src && out, "qtt_tensor_copy: null argument");
+  StreamScope scope_(as_stream(stream));
   *out = tensor_clone(src, prec, as_stream(stream));
   return QTT_OK;
   QTT_API_END
@@ -108,6 +109,7 @@ int qtt_to_full(const qtt_tensor* x, void* dst, size_t n_elems, int ordering, vo
   QTT_API_BEGIN
   QTT_REQUIRE(x && dst, "qtt_to_full: null argument");
   cudaStream_t s = as_stream(stream);
+  StreamScope scope_(s);
   Arena ar(s);
   if (x->prec == QTT_F64) to_full<double>(s, ar, x, (double*)dst, n_elems, ordering);
   else to_full<float>(s, ar, x, (float*)dst, n_elems, ordering);
@@ -120,6 +122,7 @@ int qtt_round(qtt_tensor* x, double tol, int max_rank, void* stream) {
   QTT_REQUIRE(x, "qtt_round: null tensor");
   QTT_REQUIRE(tol >= 0.0, "qtt_round: negative tolerance");
   cudaStream_t s = as_stream(stream);
+  StreamScope scope_(s);
   Arena ar(s);
   int rc = x->prec == QTT_F64 ? round_tt<double>(s, ar, x, tol, max_rank) : round_tt<float>(s, ar, x, tol, max_rank);
   QTT_CUDA(cudaStreamSynchronize(s));
@@ -132,6 +135,7 @@ int qtt_matvec(const qtt_tensor* A, const qtt_tensor* x, double tol, int max_ran
   QTT_API_BEGIN
   QTT_REQUIRE(A && x && y, "qtt_matvec: null argument");
   cudaStream_t s = as_stream(stream);
+  StreamScope scope_(s);
   qtt_tensor* out = A->prec == QTT_F64 ? product<double>(s, A, x) : product<float>(s, A, x);
   int rc = QTT_OK;
   if (tol > 0.0) {
@@ -153,6 +157,7 @@ int qtt_axpby(double alpha, const qtt_tensor* x, double beta, const qtt_tensor* 
   QTT_API_BEGIN
   QTT_REQUIRE(x && y && z, "qtt_axpby: null argument");
   cudaStream_t s = as_stream(stream);
+  StreamScope scope_(s);
   *z = x->prec == QTT_F64 ? tt_sum<double>(s, alpha, x, beta, y) : tt_sum<float>(s, (float)alpha, x, (float)beta, y);
   return QTT_OK;
   QTT_API_END
@@ -162,6 +167,7 @@ int qtt_norm(const qtt_tensor* x, double* out, void* stream) {
   QTT_API_BEGIN
   QTT_REQUIRE(x && out, "qtt_norm: null argument");
   cudaStream_t s = as_stream(stream);
+  StreamScope scope_(s);
   Arena ar(s);
   *out = x->prec == QTT_F64 ? norm<double>(s, ar, x) : norm<float>(s, ar, x);
   return QTT_OK;
@@ -173,6 +179,7 @@ int qtt_residual(const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* f, 
   QTT_REQUIRE(K && u && f && out, "qtt_residual: null argument");
   QTT_REQUIRE(K->prec == QTT_F64 && u->prec == QTT_F64 && f->prec == QTT_F64, "qtt_residual: operands must be FP64");
   cudaStream_t s = as_stream(stream);
+  StreamScope scope_(s);
   Arena ar(s);
   qtt_tensor* Ku = product<double>(s, K, u);
   qtt_tensor* r = nullptr;

@@ -106,6 +106,8 @@ struct qtt_tensor {
   int r[QTT_MAX_CORES + 1] = {0};
   void* core[QTT_MAX_CORES] = {nullptr};
   size_t cap[QTT_MAX_CORES] = {0};   // elements allocated per core
+  cudaStream_t stream = nullptr;     // stream the cores were allocated on (stream-ordered frees)
+  int sym = 0;                       // MPO known to be symmetric (set by the assembly for q = 1)
 };
 
 namespace qtt {
@@ -114,6 +116,16 @@ inline size_t esize(int prec) { return prec == QTT_F32 ? 4 : 8; }
 inline size_t core_elems(const qtt_tensor* t, int k) {
   return (size_t)t->r[k] * t->n[k] * t->m[k] * t->r[k + 1];
 }
+
+// Tensor cores come from the stream-ordered allocator on the calling
+// thread's current entry-point stream (set by StreamScope), so that freeing
+// a temporary never synchronises the device.
+cudaStream_t alloc_stream();
+struct StreamScope {
+  cudaStream_t prev;
+  explicit StreamScope(cudaStream_t s);
+  ~StreamScope();
+};
 
 qtt_tensor* tensor_alloc(int d, const int* n, const int* m, const int* r, int prec, int is_matrix);
 void tensor_free(qtt_tensor* t);

@@ -14,6 +14,13 @@ namespace qtt {
 // ---------------------------------------------------------------------------
 // Tensor memory
 // ---------------------------------------------------------------------------
+namespace {
+thread_local cudaStream_t g_alloc_stream = nullptr;
+}
+cudaStream_t alloc_stream() { return g_alloc_stream; }
+StreamScope::StreamScope(cudaStream_t s) : prev(g_alloc_stream) { g_alloc_stream = s; }
+StreamScope::~StreamScope() { g_alloc_stream = prev; }
+
 qtt_tensor* tensor_alloc(int d, const int* n, const int* m, const int* r, int prec, int is_matrix) {
   QTT_REQUIRE(d >= 1 && d <= QTT_MAX_CORES, "tensor: number of cores out of range");
   QTT_REQUIRE(prec == QTT_F64 || prec == QTT_F32, "tensor: precision must be QTT_F64 or QTT_F32");
@@ -22,6 +29,7 @@ qtt_tensor* tensor_alloc(int d, const int* n, const int* m, const int* r, int pr
   t->d = d;
   t->is_matrix = is_matrix;
   t->prec = prec;
+  t->stream = g_alloc_stream;
   for (int k = 0; k < d; ++k) {
     QTT_REQUIRE(n[k] >= 1 && (m ? m[k] : 1) >= 1 && r[k] >= 1, "tensor: sizes must be positive");
     t->n[k] = n[k];
@@ -32,7 +40,7 @@ qtt_tensor* tensor_alloc(int d, const int* n, const int* m, const int* r, int pr
     for (int k = 0; k < d; ++k) {
       size_t e = core_elems(t, k);
       t->cap[k] = e;
-      cudaError_t err = cudaMalloc(&t->core[k], std::max<size_t>(e, 1) * esize(prec));
+      cudaError_t err = cudaMallocAsync(&t->core[k], std::max<size_t>(e, 1) * esize(prec), t->stream);
       if (err != cudaSuccess) {
         cudaGetLastError();
         throw QttError(QTT_ENOMEM, "core allocation failed");
@@ -45,24 +53,28 @@ qtt_tensor* tensor_alloc(int d, const int* n, const int* m, const int* r, int pr
   return t;
 }
 
+// stream-ordered: the cores are released after the work queued so far on the
+// tensor's stream; callers free a tensor only when no other stream still uses it
 void tensor_free(qtt_tensor* t) {
   if (!t) return;
   for (int k = 0; k < t->d; ++k)
-    if (t->core[k]) cudaFree(t->core[k]);
+    if (t->core[k]) cudaFreeAsync(t->core[k], t->stream);
   delete t;
 }
 
 void tensor_reserve(qtt_tensor* t, int k, size_t elems, cudaStream_t s) {
   if (elems <= t->cap[k]) return;
-  QTT_CUDA(cudaStreamSynchronize(s));
-  if (t->core[k]) cudaFree(t->core[k]);
+  // the old core is dead: released in order on s, replaced by a new block
+  if (t->core[k]) QTT_CUDA(cudaFreeAsync(t->core[k], s));
   t->core[k] = nullptr;
-  QTT_CUDA(cudaMalloc(&t->core[k], elems * esize(t->prec)));
+  QTT_CUDA(cudaMallocAsync(&t->core[k], elems * esize(t->prec), s));
   t->cap[k] = elems;
+  t->stream = s;
 }
 
 qtt_tensor* tensor_clone(const qtt_tensor* src, int prec, cudaStream_t s) {
   qtt_tensor* t = tensor_alloc(src->d, src->n, src->m, src->r, prec, src->is_matrix);
+  t->sym = src->sym;
   for (int k = 0; k < src->d; ++k) {
     size_t e = core_elems(src, k);
     if (src->prec == prec) {

@@ -73,3 +73,19 @@ def test_solve_mixed_precision_refinement():
     assert info["rc"] == 0, info
     assert info["rel_residual"] <= 1e-9
     assert err <= 1e-7, (err, info)
+
+
+def test_batched_uneven_problems_match_oracle():
+    """Uneven batch (levels 3-5, one to three patches) through the work queue
+    with several concurrent workers: every result matches its own sparse
+    direct solution."""
+    probs = [W.plate_body_force(4), W.lshape_shear(3), W.two_patch_strip(4), W.plate_traction_smooth(5),
+             W.plate_top_traction(3, 20.0, 0.35, 1.5, 1.0)]
+    KF = [q.qtt_assemble_stiffness(p) for p in probs]
+    us, infos = q.qtt_solve_batched([k for k, _ in KF], [f for _, f in KF], nworkers=3, tol=1e-10, max_sweeps=40)
+    torch.cuda.synchronize()
+    for p, u, info in zip(probs, us, infos):
+        assert info["status"] == 0, info
+        ug = q.qtt_to_full(u).cpu().numpy()
+        ref = fem.solve_duplicated(p)
+        assert np.linalg.norm(ug - ref) / np.linalg.norm(ref) <= 1e-8
