@@ -38,6 +38,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "QTT solves/sec at rel. residual 1e-8 (L=12); fast form vs plain FP64 GPU"
 ACCEPT = 1e-8
+_T0 = time.perf_counter()
+
+
+def log(msg: str):
+    print(f"[bench {time.perf_counter() - _T0:8.1f}s] {msg}", file=sys.stderr, flush=True)
 NU_GRID = (0.2, 0.283, 0.367, 0.45)
 
 
@@ -314,12 +319,14 @@ def main():
     net, ws_info = None, None
     if args.form == "fast":
         net, ws_info = train_warm_start(args.L, args.tol, args.train_steps)
+        log(f"warm start ready: {ws_info}")
 
     def step_slice(st):
         return P[st * batch:(st + 1) * batch], probs[st * batch:(st + 1) * batch]
 
     for st in range(args.warmup):
-        run_step(args.form, *step_slice(st), net, args.tol, args.workers)
+        _, inf = run_step(args.form, *step_slice(st), net, args.tol, args.workers)
+        log(f"warm-up step {st}: sweeps {[i['sweeps'] for i in inf]} res {[i['rel_residual'] for i in inf]}")
     barrier()
 
     sampler = ClockSampler(local)
@@ -329,6 +336,7 @@ def main():
     ms = 0.0
     infos = []
     barrier()
+    torch.cuda.nvtx.range_push("timed")        # lets ncu restrict a launch list to the timed region
     for st in range(args.warmup, nsteps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -342,6 +350,7 @@ def main():
             total += 1
             accepted += int(0 < i["rel_residual"] <= args.tol)
             infos.append(i)
+    torch.cuda.nvtx.range_pop()
     barrier()
     launches = lib.qtt_kernel_launches() - launches0
     clocks = sampler.stop()
@@ -355,6 +364,7 @@ def main():
     value = acc_all / (ms_all / 1e3) if ms_all > 0 else 0.0
 
     # ---- dominant kernel class: one extra step with CUDA events per launch
+    log(f"timed: {ms_all:.1f} ms for {tot_all:.0f} solves ({acc_all:.0f} accepted)")
     lib.qtt_profile_enable(1)
     run_step(args.form, *step_slice(nsteps - 1), net, args.tol, args.workers)
     torch.cuda.synchronize()
@@ -393,6 +403,7 @@ def main():
                 "note": "event-timed over one extra step of the same workload (events bracket every launch)"}
 
     # ---- end to end through the public API, host buffers in and out
+    log(f"profiled step: dominant {dom}")
     e2e = None
     if not args.no_e2e:
         h2d = d2h = 0
@@ -417,6 +428,7 @@ def main():
             dist.destroy_process_group()
         return 0
 
+    log(f"e2e: {e2e}")
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         gs = int(statistics.median([i["sweeps"] for i in infos])) if infos else None

@@ -21,7 +21,10 @@
 #include <memory>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
+#include "contract.cuh"
 #include "tt_ops.cuh"
 
 namespace qtt {
@@ -164,6 +167,107 @@ __global__ void cg_dir_kernel(U* p, const U* r, const double* rr_new, const doub
   const double beta = old > 0.0 ? *rr_new / old : 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     p[i] = (U)((double)r[i] + beta * (double)p[i]);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent local CG (FP32): `iters` conjugate-gradient iterations on
+// B d = r in one cooperative launch.  Per iteration: the three contractions
+// of the local operator (p -> t1 -> t2 -> q) as grid-strided tile loops, the
+// dot products as block reductions with atomic accumulation, the vector
+// updates grid-strided; grid barriers separate the phases.  Device scalars:
+// acc[0] = r.r of the current direction, acc[1] = p.Bp, acc[2] = new r.r.
+// ---------------------------------------------------------------------------
+struct PcgArgs {
+  ContractArgs c1, c2, c3;
+  const float* PL;
+  const float* Ak;
+  const float* PR;
+  float* t1;
+  float* t2;
+  float* d;
+  float* r;
+  float* p;
+  float* q;
+  double* acc;
+  int N, iters;
+};
+
+__device__ double block_reduce_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = l < (int)(blockDim.x >> 5) ? red[l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  }
+  return r;   // valid in thread 0
+}
+
+__global__ void __launch_bounds__(256) pcg_kernel(PcgArgs a) {
+  cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+  __shared__ ContractSmem<float> sm;
+  __shared__ double red[32];
+  const long long it1 = contract_items(a.c1), it2 = contract_items(a.c2), it3 = contract_items(a.c3);
+  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long gstride = (long long)gridDim.x * blockDim.x;
+  for (int it = 0; it < a.iters; ++it) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && it > 0) {
+      a.acc[0] = a.acc[2];
+      a.acc[1] = 0.0;
+      a.acc[2] = 0.0;
+    }
+    for (long long w = blockIdx.x; w < it1; w += gridDim.x) contract_tile<float>(a.c1, 1.f, a.p, a.PR, 0.f, a.t1, (int)w, sm);
+    for (long long i = gtid; i < a.N; i += gstride) a.q[i] = 0.f;
+    grid.sync();
+    for (long long w = blockIdx.x; w < it2; w += gridDim.x) contract_tile<float>(a.c2, 1.f, a.t1, a.Ak, 0.f, a.t2, (int)w, sm);
+    grid.sync();
+    for (long long w = blockIdx.x; w < it3; w += gridDim.x) contract_tile<float>(a.c3, 1.f, a.PL, a.t2, 0.f, a.q, (int)w, sm);
+    grid.sync();
+    double part = 0.0;
+    for (long long i = gtid; i < a.N; i += gstride) part += (double)a.p[i] * (double)a.q[i];
+    part = block_reduce_sum(part, red);
+    if (threadIdx.x == 0) atomicAdd(&a.acc[1], part);
+    grid.sync();
+    const double pq = a.acc[1];
+    const double alpha = pq > 0.0 ? a.acc[0] / pq : 0.0;
+    part = 0.0;
+    for (long long i = gtid; i < a.N; i += gstride) {
+      a.d[i] = (float)((double)a.d[i] + alpha * (double)a.p[i]);
+      const float ri = (float)((double)a.r[i] - alpha * (double)a.q[i]);
+      a.r[i] = ri;
+      part += (double)ri * (double)ri;
+    }
+    part = block_reduce_sum(part, red);
+    if (threadIdx.x == 0) atomicAdd(&a.acc[2], part);
+    grid.sync();
+    const double rr = a.acc[0];
+    const double beta = rr > 0.0 ? a.acc[2] / rr : 0.0;
+    for (long long i = gtid; i < a.N; i += gstride) a.p[i] = (float)((double)a.r[i] + beta * (double)a.p[i]);
+    grid.sync();
+  }
+}
+
+// grid of the persistent CG: every SM holds up to two blocks (0 = the
+// cooperative launch is unavailable; computed once per process)
+int persistent_cg_grid() {
+  static int grid = -1;
+  if (grid >= 0) return grid;
+  int dev = 0, coop = 0, sms = 0, nb = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pcg_kernel, 256, 0) != cudaSuccess || !coop || nb < 1) {
+    cudaGetLastError();
+    grid = 0;
+  } else {
+    grid = sms * std::min(nb, 2);
+  }
+  return grid;
 }
 
 // deterministic residual proxy when none is given: smooth sign-varying values
@@ -445,16 +549,46 @@ struct Amen {
       double* rr_new = sc4 + 1;
       double* pq = sc4 + 2;
       dotp<U>(s, r, r, N, rr_old);
-      for (int j = 0; j < m; ++j) {
-        Arena ij(s);
-        apply_local<U>(s, ij, PL, r0, r0, Ak, R0, n, R1, PR, r1, r1, p, qv);
-        dotp<U>(s, p, qv, N, pq);
-        cg_step_kernel<U><<<grid_for(N), 256, 0, s>>>(d, r, p, qv, rr_old, pq, N);
-        QTT_CHECK_LAUNCH();
-        dotp<U>(s, r, r, N, rr_new);
-        cg_dir_kernel<U><<<grid_for(N), 256, 0, s>>>(p, r, rr_new, rr_old, N);
-        QTT_CHECK_LAUNCH();
-        std::swap(rr_old, rr_new);
+      if (sizeof(U) == 4 && persistent_cg_grid() > 0) {
+        // all m iterations in one cooperative launch
+        const int grid = persistent_cg_grid();
+        PcgArgs pa{};
+        int dx[3] = {r0, n, r1}, dR[3] = {r1, R1, r1}, d1[4] = {r0, n, r1, R1}, dA[4] = {R0, n, n, R1};
+        int dL[3] = {r0, R0, r0}, d2[4] = {r0, r1, R0, n};
+        bool ok = plan_contract("cjd,bBd->cjbB", dx, dR, 4, 0, pa.c1) &&
+                  plan_contract("cjbB,AijB->cbAi", d1, dA, 4, 0, pa.c2) &&
+                  plan_contract("aAc,cbAi->aib", dL, d2, 4, grid, pa.c3);
+        QTT_REQUIRE(ok, "persistent CG: contraction plan failed");
+        float* t1 = sc.alloc<float>((size_t)r0 * n * r1 * R1);
+        float* t2 = sc.alloc<float>((size_t)r0 * r1 * R0 * n);
+        QTT_CUDA(cudaMemsetAsync(sc4 + 1, 0, 2 * sizeof(double), s));
+        pa.PL = reinterpret_cast<const float*>(PL);
+        pa.Ak = reinterpret_cast<const float*>(Ak);
+        pa.PR = reinterpret_cast<const float*>(PR);
+        pa.t1 = t1;
+        pa.t2 = t2;
+        pa.d = reinterpret_cast<float*>(d);
+        pa.r = reinterpret_cast<float*>(r);
+        pa.p = reinterpret_cast<float*>(p);
+        pa.q = reinterpret_cast<float*>(qv);
+        pa.acc = sc4;
+        pa.N = N;
+        pa.iters = m;
+        void* kargs[] = {&pa};
+        QTT_CUDA(cudaLaunchCooperativeKernel((void*)pcg_kernel, grid, 256, kargs, 0, s));
+        count_launch();
+      } else {
+        for (int j = 0; j < m; ++j) {
+          Arena ij(s);
+          apply_local<U>(s, ij, PL, r0, r0, Ak, R0, n, R1, PR, r1, r1, p, qv);
+          dotp<U>(s, p, qv, N, pq);
+          cg_step_kernel<U><<<grid_for(N), 256, 0, s>>>(d, r, p, qv, rr_old, pq, N);
+          QTT_CHECK_LAUNCH();
+          dotp<U>(s, r, r, N, rr_new);
+          cg_dir_kernel<U><<<grid_for(N), 256, 0, s>>>(p, r, rr_new, rr_old, N);
+          QTT_CHECK_LAUNCH();
+          std::swap(rr_old, rr_new);
+        }
       }
       if (sizeof(U) != sizeof(T)) {
         convert<U, T>(s, d, wT, N);

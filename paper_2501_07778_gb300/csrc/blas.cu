@@ -6,6 +6,7 @@
 #include <string>
 
 #include "common.cuh"
+#include "contract.cuh"
 
 namespace qtt {
 
@@ -101,6 +102,27 @@ __global__ void scale_matrix_kernel(int M, int N, T* C, int ldc, long long sC, i
 }
 
 // Small-K / skinny fallback is not needed: the tile kernel handles any shape.
+
+// Work-item loop over the strided contraction (contract.cuh): one block per
+// output tile (and K split), grid-strided.
+template <typename T>
+__global__ void __launch_bounds__(256) contract_kernel(ContractArgs a, T alpha, const T* __restrict__ A,
+                                                       const T* __restrict__ B, T beta, T* __restrict__ C,
+                                                       long long items) {
+  __shared__ ContractSmem<T> sm;
+  for (long long it = blockIdx.x; it < items; it += gridDim.x) contract_tile<T>(a, alpha, A, B, beta, C, (int)it, sm);
+}
+
+// C = beta C over the strided output (before split-K accumulation)
+template <typename T>
+__global__ void contract_scale_kernel(ContractArgs a, T* C, T beta) {
+  long long total = (long long)a.M * a.N * a.batch;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    T* c = C + contract_out_off(a, t);
+    *c = (beta == T(0)) ? T(0) : beta * (*c);
+  }
+}
 
 constexpr int PMAX = 24;
 struct PermArgs {
@@ -372,6 +394,27 @@ void einsum(cudaStream_t s, Arena& ar, const char* spec, const T* A, const int* 
   const long long nFA = prod_of(freeA, size_of), nFB = prod_of(freeB, size_of), nK = prod_of(contr, size_of),
                   nBt = prod_of(batch, size_of);
   QTT_REQUIRE(nBt <= 65535, "einsum: batch too large");
+  if (nFA == 0 || nFB == 0 || nBt == 0) return;
+  {
+    ContractArgs ca{};
+    if (plan_contract(spec, dA, dB, (int)sizeof(T), 304, ca)) {
+      const long long items = contract_items(ca);
+      ProfToken pt = prof_begin(sizeof(T) == 8 ? PROF_GEMM_F64 : PROF_GEMM_F32, s);
+      if (ca.splits > 1) {
+        contract_scale_kernel<T><<<grid_for((long long)ca.M * ca.N * ca.batch), 256, 0, s>>>(ca, C, beta);
+        QTT_CHECK_LAUNCH();
+      }
+      const int grid = (int)std::min<long long>(items, 1LL << 30);
+      contract_kernel<T><<<grid, 256, 0, s>>>(ca, alpha, A, B, beta, C, items);
+      QTT_CHECK_LAUNCH();
+      if (pt.ev) {
+        const double mn = (double)ca.M * ca.N, bt = (double)ca.batch;
+        prof_end(pt, s, 2.0 * mn * ca.K * bt,
+                 bt * sizeof(T) * ((double)ca.M * ca.K + (double)ca.K * ca.N + (beta == T(0) ? 1.0 : 2.0) * mn));
+      }
+      return;
+    }
+  }
   // operand A
   const T* Ause = A;
   bool tA = false;
@@ -421,6 +464,110 @@ void einsum(cudaStream_t s, Arena& ar, const char* spec, const T* A, const int* 
     std::vector<int> p = perm_of(have, lc);
     permute<T>(s, tmp, C, (int)have.size(), dims.data(), p.data(), alpha, beta);
   }
+}
+
+
+// ---------------------------------------------------------------------------
+// Contraction planner (contract.cuh)
+// ---------------------------------------------------------------------------
+bool plan_contract(const char* spec, const int* dA, const int* dB, int sizeof_T, long long min_items,
+                   ContractArgs& ca) {
+  std::string sp(spec);
+  size_t comma = sp.find(','), arrow = sp.find("->");
+  QTT_REQUIRE(comma != std::string::npos && arrow != std::string::npos, "contract: bad spec");
+  std::string la = sp.substr(0, comma), lb = sp.substr(comma + 1, arrow - comma - 1), lc = sp.substr(arrow + 2);
+  int size_of[256];
+  for (int i = 0; i < 256; ++i) size_of[i] = -1;
+  for (size_t k = 0; k < la.size(); ++k) size_of[(unsigned char)la[k]] = dA[k];
+  for (size_t k = 0; k < lb.size(); ++k) {
+    int& z = size_of[(unsigned char)lb[k]];
+    QTT_REQUIRE(z < 0 || z == dB[k], std::string("contract: size mismatch for label ") + lb[k] + " in " + sp);
+    z = dB[k];
+  }
+  std::string batch, contr, freeA, freeB;
+  for (char c : la) {
+    bool inB = lb.find(c) != std::string::npos, inC = lc.find(c) != std::string::npos;
+    if (inB && inC) batch += c;
+    else if (inB) contr += c;
+    else if (inC) freeA += c;
+    else QTT_REQUIRE(false, "contract: label only in A");
+  }
+  for (char c : lb)
+    if (la.find(c) == std::string::npos) {
+      QTT_REQUIRE(lc.find(c) != std::string::npos, "contract: label only in B");
+      freeB += c;
+    }
+  if (freeA.size() > 4 || freeB.size() > 4 || contr.size() > 4 || batch.size() > 4) return false;
+  auto prod = [&](const std::string& g) {
+    long long p = 1;
+    for (char c : g) p *= size_of[(unsigned char)c];
+    return p;
+  };
+  const long long nFA = prod(freeA), nFB = prod(freeB), nK = prod(contr), nBt = prod(batch);
+  if (nFA >= (1LL << 31) || nFB >= (1LL << 31) || nK >= (1LL << 31) || nBt > 65535) return false;
+  auto strides = [&](const std::string& lab) {
+    std::vector<long long> st(256, 0);
+    long long acc = 1;
+    for (char c : lab) {
+      st[(unsigned char)c] = acc;
+      acc *= size_of[(unsigned char)c];
+    }
+    return st;
+  };
+  std::vector<long long> sa = strides(la), sb = strides(lb), sc = strides(lc);
+  auto sort_by = [&](std::string g, const std::vector<long long>& st) {
+    std::stable_sort(g.begin(), g.end(), [&](char x, char y) { return st[(unsigned char)x] < st[(unsigned char)y]; });
+    return g;
+  };
+  const std::string gA = sort_by(freeA, sa), gB = sort_by(freeB, sb), gK = sort_by(contr, sa);
+  auto make = [&](const std::string& g, const std::vector<long long>& st) {
+    IdxMap m{};
+    m.cnt = (int)g.size();
+    for (int t = 0; t < m.cnt; ++t) {
+      m.n[t] = size_of[(unsigned char)g[t]];
+      m.s[t] = st[(unsigned char)g[t]];
+    }
+    if (m.cnt == 0) {
+      m.cnt = 1;
+      m.n[0] = 1;
+      m.s[0] = 0;
+    }
+    return m;
+  };
+  ca = ContractArgs{};
+  ca.M = (int)nFA;
+  ca.N = (int)nFB;
+  ca.K = (int)nK;
+  ca.batch = (int)nBt;
+  ca.am = make(gA, sa);
+  ca.cm = make(gA, sc);
+  ca.bn = make(gB, sb);
+  ca.cn = make(gB, sc);
+  ca.ak = make(gK, sa);
+  ca.bk = make(gK, sb);
+  ca.ab = make(batch, sa);
+  ca.bb = make(batch, sb);
+  ca.cb = make(batch, sc);
+  ca.a_m_fast = (ca.am.s[0] == 1) || !(ca.ak.s[0] == 1);
+  ca.b_n_fast = (ca.bn.s[0] == 1) && !(ca.bk.s[0] == 1);
+  ca.tiles_m = (int)((nFA + CT_BM - 1) / CT_BM);
+  ca.tiles_n = (int)((nFB + CT_BN - 1) / CT_BN);
+  const long long tiles = (long long)ca.tiles_m * ca.tiles_n * nBt;
+  int splits = 1;
+  if (tiles < min_items && nK >= 256) {
+    long long want = (min_items + tiles - 1) / tiles;
+    splits = (int)std::min<long long>(want, (nK + 127) / 128);
+    splits = std::max(1, splits);
+  }
+  int kchunk = (int)std::max<long long>(1, nK);
+  if (splits > 1) {
+    kchunk = (int)(((nK + splits - 1) / splits + CT_BK - 1) / CT_BK * CT_BK);
+    splits = (int)((nK + kchunk - 1) / kchunk);
+  }
+  ca.splits = splits;
+  ca.kchunk = kchunk;
+  (void)sizeof_T;
+  return true;
 }
 
 #define QTT_INST(T)                                                                                              \

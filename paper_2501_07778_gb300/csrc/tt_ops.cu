@@ -2,6 +2,7 @@
 // format, the core-by-core MPO x MPS product, sums, orthogonalisation, norms
 // and rounding (Oseledets 2011, Alg. 2).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -18,7 +19,32 @@ namespace {
 thread_local cudaStream_t g_alloc_stream = nullptr;
 }
 cudaStream_t alloc_stream() { return g_alloc_stream; }
-StreamScope::StreamScope(cudaStream_t s) : prev(g_alloc_stream) { g_alloc_stream = s; }
+
+// The engine allocates and frees many small blocks per core step through the
+// stream-ordered allocator.  With the pool's default release threshold (0)
+// every synchronisation returns the cached memory to the driver and the next
+// allocation maps it again, which serialises concurrent solves; keep it cached.
+static void keep_pool_memory() {
+  static std::atomic<int> done_mask{0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev >= 31) {
+    cudaGetLastError();
+    return;
+  }
+  if (done_mask.load() & (1 << dev)) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  cudaGetLastError();
+  done_mask.fetch_or(1 << dev);
+}
+
+StreamScope::StreamScope(cudaStream_t s) : prev(g_alloc_stream) {
+  keep_pool_memory();
+  g_alloc_stream = s;
+}
 StreamScope::~StreamScope() { g_alloc_stream = prev; }
 
 qtt_tensor* tensor_alloc(int d, const int* n, const int* m, const int* r, int prec, int is_matrix) {
