@@ -14,6 +14,7 @@
 namespace qtt {
 int solve(const qtt_tensor* K, const qtt_tensor* f, const qtt_tensor* x0, const qtt_tensor* z0,
           const qtt_solve_opts* opts, qtt_tensor** xout, qtt_solve_info* info, cudaStream_t s);
+void set_gpu_share(int n);
 }
 
 using namespace qtt;
@@ -45,6 +46,7 @@ extern "C" int qtt_solve_batched(int count, const qtt_tensor* const* K, const qt
     auto worker = [&](int w) {
       cudaSetDevice(dev);
       StreamScope scope_(streams[w]);
+      set_gpu_share(W);
       for (;;) {
         const int i = next.fetch_add(1);
         if (i >= count) break;
