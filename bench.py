@@ -139,7 +139,7 @@ def solve_kw(form: str, tol: float):
     # no outer refinement step in the timed workload: at L = 12 its FP64
     # rounding of the rank ~4500 residual costs more than a solve; a solve that
     # ends above tol is counted as not accepted
-    return dict(tol=tol, precision=q.QTT_MIXED, kick_rank=8, max_sweeps=MAX_SWEEPS, refine_max=0)
+    return dict(tol=tol, precision=q.QTT_MIXED, kick_rank=8, max_sweeps=MAX_SWEEPS, refine_max=-1)
 
 
 def run_step(form, params, probs, net, tol, workers):
@@ -160,9 +160,12 @@ def train_warm_start(L: int, tol: float, steps: int):
     from paper_2501_07778_gb300 import QTT_F32, QTT_MIXED
     from paper_2501_07778_gb300 import warmstart as ws
     t0 = time.perf_counter()
-    basis64 = ws.basis_solutions(L, NU_GRID, tol=tol, precision=QTT_MIXED, kick_rank=8, max_sweeps=40)
+    log(f"warm start: {2 * len(NU_GRID)} basis solves at L={L}")
+    basis64 = ws.basis_solutions(L, NU_GRID, tol=tol, precision=QTT_MIXED, kick_rank=8, max_sweeps=MAX_SWEEPS,
+                                 refine_max=-1)
     basis = [b.copy(prec=QTT_F32) for b in basis64]
     t1 = time.perf_counter()
+    log(f"warm start: basis solves took {t1 - t0:.1f} s; training {steps} steps")
     modes = W.qtt_modes(W.plate_top_traction(L, 1.0, 0.3, 1.0, 0.0))
     net = ws.WarmStartMLP(modes, r=16, H=256, seed=0)
     P, coef = ws.dataset(1, 2000, NU_GRID)
@@ -319,6 +322,7 @@ def main():
     batch = args.batch or (2 if args.form == "fast" else 1)
     nsteps = args.warmup + args.steps
     P, probs = workload(args.L, nsteps * batch, rank, world)
+    log(f"library ready; form {args.form}, L={args.L}, {batch} solves per step, {nsteps} steps")
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > 129 MB L2
 
@@ -377,7 +381,7 @@ def main():
     torch.cuda.synchronize()
     lib.qtt_profile_enable(0)
     classes = {0: "gemm_f64", 1: "gemm_f32", 2: "core_product", 3: "qr_panel", 4: "jacobi_svd", 5: "lu_panel",
-               6: "permute"}
+               6: "permute", 7: "to_full", 8: "pcg_f32"}
     prof = {}
     for cid, nm in classes.items():
         a, f_, b_, n_ = C.c_double(), C.c_double(), C.c_double(), C.c_longlong()
@@ -395,7 +399,7 @@ def main():
     if dom in ("gemm_f64", "qr_panel", "jacobi_svd", "lu_panel"):
         bound, peak, unit, src = "alu", 1.25, "TFLOP/s", "FP64 rate of GB300 (2 DFMA/SM/clk x 152 SMs x 2.07 GHz)"
         achieved = d["gflop"] / 1e3 / sec if sec > 0 else 0.0
-    elif dom == "gemm_f32":
+    elif dom in ("gemm_f32", "pcg_f32"):
         bound, peak, unit = "alu", 152 * 128 * 2 * 2.07e9 / 1e12, "TFLOP/s"
         src = "FP32 SIMT: 152 SMs x 128 lanes x 2 flops x 2.07 GHz"
         achieved = d["gflop"] / 1e3 / sec if sec > 0 else 0.0

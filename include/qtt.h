@@ -188,7 +188,8 @@ typedef struct {
   int local_restart;      /* GMRES restart length for larger local systems (<= 0: 40) */
   int local_max_cycles;   /* GMRES restart cycles per local solve (<= 0: 8) */
   int precision;          /* QTT_F64, QTT_F32 or QTT_MIXED */
-  int refine_max;         /* QTT_MIXED: maximum refinement steps (<= 0: 6) */
+  int refine_max;         /* QTT_MIXED: maximum refinement steps (0: 4; < 0: none,
+                             the FP64 global check of the sweeps decides) */
   double inner_tol;       /* QTT_MIXED: tolerance of each FP32 inner solve (<= 0: 1e-5) */
   int verbose;            /* print per-sweep progress to stderr */
 } qtt_solve_opts;
@@ -294,7 +295,8 @@ unsigned long long qtt_kernel_launches(void);
  * events on its stream and record its algorithmic flops and bytes (adds
  * launch overhead; off by default).  Classes: 0 FP64 GEMM, 1 FP32 GEMM,
  * 2 MPO x MPS core product, 3 Householder panel, 4 Jacobi SVD, 5 LU panel,
- * 6 permutation, 7 full expansion. */
+ * 6 permutation, 7 full expansion, 8 persistent FP32 local CG (one launch runs
+ * all iterations of a CG cycle). */
 int qtt_profile_enable(int on);
 
 /* Sum of event-timed milliseconds, algorithmic flops and bytes, and launch

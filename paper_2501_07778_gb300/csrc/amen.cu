@@ -647,8 +647,20 @@ struct Amen {
         pa.N = N;
         pa.iters = m;
         void* kargs[] = {&pa};
+        ProfToken pt = prof_begin(PROF_PCG, s);
         QTT_CUDA(cudaLaunchCooperativeKernel((void*)pcg_kernel, grid, 256, kargs, 0, s));
         count_launch();
+        if (pt.ev) {
+          // per iteration: the three contractions of B p, three dot products
+          // and the d, r, p updates; bytes: the three operator factors read
+          // once (they stay in L2 across iterations, so this is per launch),
+          // plus the vectors and contraction intermediates written and read
+          const double fl = 2.0 * ((double)r0 * n * r1 * R1 * r1 + (double)r0 * r1 * R0 * n * n * R1 +
+                                   (double)r0 * R0 * r0 * r1 * n) + 16.0 * N;
+          const double ops = (double)r0 * R0 * r0 + (double)R0 * n * n * R1 + (double)r1 * R1 * r1;
+          const double vec = 2.0 * ((double)r0 * n * r1 * R1 + (double)r0 * r1 * R0 * n) + 12.0 * N;
+          prof_end(pt, s, fl * m, 4.0 * (ops + vec * m));
+        }
       } else {
         for (int j = 0; j < m; ++j) {
           Arena ij(s);
@@ -1009,7 +1021,7 @@ int solve(const qtt_tensor* K, const qtt_tensor* f, const qtt_tensor* x0, const 
     // (QTT matvec and sum in FP64) decides; if it is above tol, r is rounded
     // in FP64, K d = r is solved the same way and u <- round64(u + d).
     const double inner = o.inner_tol > 0 ? o.inner_tol : 1e-3;
-    const int refine_max = o.refine_max > 0 ? o.refine_max : 4;
+    const int refine_max = o.refine_max > 0 ? o.refine_max : (o.refine_max < 0 ? 0 : 4);
     Tptr u = x0 ? own(tensor_clone(x0, QTT_F64, s)) : default_x0(s, f, QTT_F64);
     Tptr z = z0 ? own(tensor_clone(z0, QTT_F64, s)) : default_z0(s, f, rho, QTT_F64);
     rc = amen_run<double>(s, K, f, u.get(), z.get(), o.tol, o, inf, true);
