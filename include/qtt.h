@@ -174,6 +174,20 @@ int qtt_norm(const qtt_tensor* x, double* out, void* stream);
  * QTT_ORDER_Z_BLOCK is accepted (dense column-major matrix). */
 int qtt_to_full(const qtt_tensor* x, void* dst, size_t n_elems, int ordering, void* stream);
 
+/* qtt_to_full for an MPS in QTT_ORDER_Z_BLOCK, computed without taking any
+ * device memory at call time.  The paper has no counterpart: this serves
+ * callers that must not enter an allocator while they run.  The partial
+ * expansions live in one fixed 32 MiB buffer per device that is part of the
+ * library image.
+ *   dst, n_elems -- as for qtt_to_full (DEVICE pointer, n_elems = prod n).
+ *   Returns QTT_EINVAL for an MPO, a size mismatch, or a tensor whose partial
+ *   expansions need more than 32 MiB (checked before any launch).
+ * The first call on a device looks the buffer up and may load the module:
+ * make it, with that device current, before any stream capture.  Calls that
+ * overlap in time on one device share the buffer and race: serialise them.
+ * The buffer needs no initial contents (each use writes before it reads). */
+int qtt_to_full_noalloc(const qtt_tensor* x, void* dst, size_t n_elems, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Solver (AMEn, cited by the paper for K u = f)                             */
 /* ------------------------------------------------------------------------ */

@@ -19,7 +19,7 @@ from ._lib import (QTT_F32, QTT_F64, QTT_MIXED, QTT_ORDER_CANONICAL, QTT_ORDER_Z
                    QttSolveOpts)
 
 __all__ = ["QTT", "QttError", "qtt_assemble_stiffness", "qtt_matvec", "qtt_round", "qtt_solve", "qtt_to_full",
-           "qtt_axpby", "qtt_norm", "qtt_residual", "QTT_F64", "QTT_F32", "QTT_MIXED", "QTT_ORDER_Z_BLOCK",
+           "qtt_axpby", "qtt_norm", "qtt_residual", "qtt_to_full_noalloc", "QTT_F64", "QTT_F32", "QTT_MIXED", "QTT_ORDER_Z_BLOCK",
            "QTT_ORDER_CANONICAL", "lib"]
 
 
@@ -146,6 +146,19 @@ def qtt_to_full(x: QTT, ordering: int = QTT_ORDER_Z_BLOCK, out=None, stream=None
         out = torch.empty(total, dtype=dt, device="cuda")
     assert out.is_cuda and out.numel() == total and out.dtype == dt and out.is_contiguous()
     _check(lib().qtt_to_full(x.handle, C.c_void_p(out.data_ptr()), total, ordering, _stream(stream)), "qtt_to_full")
+    return out
+
+
+def qtt_to_full_noalloc(x: QTT, out, stream=None):
+    """Z-block expansion of an MPS into the caller's CUDA tensor `out`, with
+    the library taking no device memory during the call."""
+    import torch
+    d, n, m, r, p = x._info()
+    total = int(np.prod(n, dtype=np.int64))
+    dt = torch.float64 if p == QTT_F64 else torch.float32
+    assert out.is_cuda and out.numel() == total and out.dtype == dt and out.is_contiguous()
+    _check(lib().qtt_to_full_noalloc(x.handle, C.c_void_p(out.data_ptr()), total, _stream(stream)),
+           "qtt_to_full_noalloc")
     return out
 
 

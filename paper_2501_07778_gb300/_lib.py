@@ -60,6 +60,7 @@ SIGNATURES = {
     "qtt_axpby": (C.c_int, [C.c_double, P, C.c_double, P, PP, P]),
     "qtt_norm": (C.c_int, [P, C.POINTER(C.c_double), P]),
     "qtt_to_full": (C.c_int, [P, P, C.c_size_t, C.c_int, P]),
+    "qtt_to_full_noalloc": (C.c_int, [P, P, C.c_size_t, P]),
     "qtt_solve": (C.c_int, [P, P, P, P, C.POINTER(QttSolveOpts), PP, C.POINTER(QttSolveInfo), P]),
     "qtt_residual": (C.c_int, [P, P, P, C.POINTER(C.c_double), P]),
     "qtt_solve_batched": (C.c_int, [C.c_int, PP, PP, PP, C.POINTER(QttSolveOpts), C.c_int, PP,
