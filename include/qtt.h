@@ -188,6 +188,19 @@ int qtt_to_full(const qtt_tensor* x, void* dst, size_t n_elems, int ordering, vo
  * The buffer needs no initial contents (each use writes before it reads). */
 int qtt_to_full_noalloc(const qtt_tensor* x, void* dst, size_t n_elems, void* stream);
 
+/* Rank-`rank` FP64 approximation r~ of the residual f - K u (K an MPO, u and
+ * f MPS, all FP64) by randomized TT rounding, randomize-then-orthogonalize
+ * (Al Daas et al., SIAM J. Sci. Comput. 2023), of the structured sum: the
+ * cores of K u are never formed.  This is the residual step of the outer
+ * refinement in qtt_solve.  r~ is the orthogonal projection of f - K u onto
+ * the span of its left-orthonormal factors, so ||f - K u - r~||^2 =
+ * ||f - K u||^2 - ||r~||^2; it equals f - K u (up to rounding) when `rank`
+ * reaches the ranks of the sum.  `seed` selects the Gaussian sketch;
+ * *kept_norm (may be NULL) receives ||r~||.  Creates *r (left-orthonormal
+ * cores, the norm in the last).  QTT_EINVAL on shape or precision mismatch. */
+int qtt_round_residual(const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* f, int rank,
+                       unsigned long long seed, double* kept_norm, qtt_tensor** r, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Solver (AMEn, cited by the paper for K u = f)                             */
 /* ------------------------------------------------------------------------ */
@@ -202,9 +215,10 @@ typedef struct {
   int local_restart;      /* GMRES restart length for larger local systems (<= 0: 40) */
   int local_max_cycles;   /* GMRES restart cycles per local solve (<= 0: 8) */
   int precision;          /* QTT_F64, QTT_F32 or QTT_MIXED */
-  int refine_max;         /* QTT_MIXED: maximum refinement steps (0: 4; < 0: none,
-                             the FP64 global check of the sweeps decides) */
-  double inner_tol;       /* QTT_MIXED: tolerance of each FP32 inner solve (<= 0: 1e-5) */
+  int refine_max;         /* QTT_F64 / QTT_MIXED: maximum outer refinement steps
+                             (0: 4; < 0: none, the sweeps alone decide) */
+  double inner_tol;       /* relative tolerance of each refinement's correction
+                             solve (<= 0: 1e-3) */
   int verbose;            /* print per-sweep progress to stderr */
 } qtt_solve_opts;
 
@@ -212,9 +226,9 @@ typedef struct {
   int status;             /* QTT_OK or the returned error code */
   int sweeps;             /* total AMEn sweeps (all inner solves) */
   int local_solves;       /* local systems solved */
-  int local_iters;        /* GMRES iterations over all local solves */
+  int local_iters;        /* Krylov iterations over all local solves */
   int max_rank;           /* largest solution rank */
-  int refinements;        /* QTT_MIXED outer steps */
+  int refinements;        /* outer refinement steps taken */
   double max_local_res;   /* last sweep's maximum local relative residual */
   double rel_residual;    /* FP64 ||f - K u|| / ||f|| (computed when tol > 0) */
   double erank;           /* effective rank of the solution (Section 4) */
@@ -228,9 +242,16 @@ typedef struct {
  * truncate it at the smallest rank whose local residual stays <= tol /
  * sqrt(D), enrich the basis with the residual projected on the proxy's
  * interfaces, and update the interfaces; stop when the sweep's maximum local
- * residual is <= tol.  With QTT_MIXED the sweeps run in FP32 on an FP32 copy
- * of K and the residual f - K u is formed and rounded in FP64 between
- * solves (iterative refinement).  Creates *x; info may be NULL.  Returns
+ * residual is <= tol (or, for QTT_F64 / QTT_MIXED, once the FP64 global
+ * relative residual is <= tol).  Local systems above local_direct_max use
+ * (Jacobi-preconditioned) CG for a symmetric K, restarted GMRES otherwise;
+ * with QTT_MIXED their Krylov cycles apply an FP32 copy of the local
+ * operator while interfaces, residuals and truncations stay FP64.  With
+ * QTT_F64 / QTT_MIXED, sweeps that stall above tol hand over to outer
+ * iterative refinement: the residual f - K u is formed by the FP64 QTT
+ * matvec and rounded in FP64 (qtt_round_residual), K d = r is solved the
+ * same way to inner_tol, and u <- round(u + d).  QTT_F32 runs everything in
+ * FP32 without refinement.  Creates *x; info may be NULL.  Returns
  * QTT_ENOCONV (with *x valid) if max_sweeps / refine_max run out. */
 int qtt_solve(const qtt_tensor* K, const qtt_tensor* f, const qtt_tensor* x0,
               const qtt_tensor* z0, const qtt_solve_opts* opts, qtt_tensor** x,

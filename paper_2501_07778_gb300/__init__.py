@@ -19,7 +19,7 @@ from ._lib import (QTT_F32, QTT_F64, QTT_MIXED, QTT_ORDER_CANONICAL, QTT_ORDER_Z
                    QttSolveOpts)
 
 __all__ = ["QTT", "QttError", "qtt_assemble_stiffness", "qtt_matvec", "qtt_round", "qtt_solve", "qtt_to_full",
-           "qtt_axpby", "qtt_norm", "qtt_residual", "qtt_to_full_noalloc", "QTT_F64", "QTT_F32", "QTT_MIXED", "QTT_ORDER_Z_BLOCK",
+           "qtt_axpby", "qtt_norm", "qtt_residual", "qtt_round_residual", "qtt_to_full_noalloc", "QTT_F64", "QTT_F32", "QTT_MIXED", "QTT_ORDER_Z_BLOCK",
            "QTT_ORDER_CANONICAL", "lib"]
 
 
@@ -189,6 +189,15 @@ def qtt_residual(K: QTT, u: QTT, f: QTT, stream=None) -> float:
     v = C.c_double()
     _check(lib().qtt_residual(K.handle, u.handle, f.handle, C.byref(v), _stream(stream)), "qtt_residual")
     return v.value
+
+
+def qtt_round_residual(K: QTT, u: QTT, f: QTT, rank: int, seed: int = 0, stream=None):
+    """Randomized rank-`rank` FP64 rounding of f - K u; returns (r, ||r||)."""
+    h = C.c_void_p()
+    kept = C.c_double()
+    _check(lib().qtt_round_residual(K.handle, u.handle, f.handle, rank, seed, C.byref(kept), C.byref(h),
+                                    _stream(stream)), "qtt_round_residual")
+    return QTT(h), kept.value
 
 
 def make_problem_struct(prob, tol: float = 0.0):

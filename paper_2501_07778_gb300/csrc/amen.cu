@@ -354,6 +354,7 @@ struct Amen {
   int max_rank, kick, max_sweeps, ndir, restart, cycles, verbose;
   bool mixed_local = false;   // FP32 operator inside the local GMRES cycles
   double global_check = 0.0;  // > 0: check the FP64 global residual once max local <= global_check * tol
+  bool stall_exit = false;    // stop when two sweeps in a row fail to halve the best max local residual
   // interfaces: PhiR[k] (bond k), k = 0..D
   std::vector<DBuf<T>> XAX_R, XY_R, ZAX_R, ZY_R;
   DBuf<T> XAX_L, XY_L, ZAX_L, ZY_L, XAX_Ln, XY_Ln, ZAX_Ln, ZY_Ln;
@@ -708,6 +709,9 @@ struct Amen {
     const double tloc = global_stop ? 0.25 * tol : tol;
     const double delta = tloc / std::sqrt((double)D);
     int status = QTT_ENOCONV;
+    const auto t_start = std::chrono::steady_clock::now();
+    double best_res = 1e300, checked_at = 1e300;
+    int stalled = 0;
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
       {
         Arena sc(s);
@@ -849,8 +853,9 @@ struct Amen {
         info->max_local_res = max_res;
       }
       if (verbose) {
-        fprintf(stderr, "[qtt_solve %s] sweep %d max local res %.3e ranks", sizeof(T) == 8 ? "f64" : "f32", sweep + 1,
-                max_res);
+        QTT_CUDA(cudaStreamSynchronize(s));
+        fprintf(stderr, "[qtt_solve %s %.2fs] sweep %d max local res %.3e ranks", sizeof(T) == 8 ? "f64" : "f32",
+                std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count(), sweep + 1, max_res);
         for (int k = 0; k <= D; ++k) fprintf(stderr, " %d", x->r[k]);
         fprintf(stderr, "\n");
       }
@@ -862,14 +867,30 @@ struct Amen {
       // global one is already below (the local ones are projections of the
       // last iterate's residual, measured before each core's update): once
       // they are within global_check x tol, the FP64 global residual decides.
-      if (sizeof(T) == 8 && global_check > 0 && max_res <= global_check * tol) {
+      // It is measured again only after the local residuals have halved.
+      if (sizeof(T) == 8 && global_check > 0 && max_res <= global_check * tol && max_res <= 0.5 * checked_at) {
+        checked_at = max_res;
         const double rel = residual64(s, A, x, y);
         if (info) info->rel_residual = rel;
-        if (verbose) fprintf(stderr, "[qtt_solve f64] sweep %d global FP64 rel residual %.3e\n", sweep + 1, rel);
+        if (verbose)
+          fprintf(stderr, "[qtt_solve f64 %.2fs] sweep %d global FP64 rel residual %.3e\n",
+                  std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count(), sweep + 1, rel);
         if (rel <= tol) {
           status = QTT_OK;
           break;
         }
+      }
+      // At large L the local systems are too ill-conditioned for the local
+      // Krylov solves to reach tol, and the sweeps stall a little above it;
+      // the caller's outer refinement takes over from there.
+      // (counted only within 100 x tol: farther out, the residual can stay
+      // level for a few sweeps while the ranks grow)
+      if (max_res <= 0.5 * best_res) {
+        best_res = max_res;
+        stalled = 0;
+      } else if (stall_exit && max_res <= 1e2 * tol && ++stalled >= 2) {
+        if (verbose) fprintf(stderr, "[qtt_solve] sweeps stalled at max local res %.3e\n", max_res);
+        break;
       }
     }
     return status;
@@ -906,7 +927,8 @@ Tptr default_z0(cudaStream_t s, const qtt_tensor* f, int rho, int prec) {
 
 template <typename T>
 int amen_run(cudaStream_t s, const qtt_tensor* K, const qtt_tensor* f, qtt_tensor* x, qtt_tensor* z, double tol,
-             const qtt_solve_opts& o, qtt_solve_info* info, bool mixed_local = false) {
+             const qtt_solve_opts& o, qtt_solve_info* info, bool mixed_local = false, bool stall_exit = false,
+             double global_check = 30.0) {
   Arena ar(s);
   Amen<T> am(s, ar);
   am.A = K;
@@ -924,7 +946,8 @@ int amen_run(cudaStream_t s, const qtt_tensor* K, const qtt_tensor* f, qtt_tenso
   am.verbose = o.verbose;
   am.info = info;
   am.mixed_local = mixed_local;
-  am.global_check = 30.0;
+  am.global_check = global_check;
+  am.stall_exit = stall_exit;
   am.dscal = ar.alloc<double>(4);
   int rc = am.run();
   QTT_CUDA(cudaStreamSynchronize(s));
@@ -994,61 +1017,73 @@ int solve(const qtt_tensor* K, const qtt_tensor* f, const qtt_tensor* x0, const 
   std::memset(inf, 0, sizeof(*inf));
   const int rho = o.kick_rank > 0 ? o.kick_rank : 8;
   int rc = QTT_OK;
-  if (o.precision == QTT_F64 || o.precision == QTT_F32) {
-    const int prec = o.precision;
-    QTT_REQUIRE(prec == QTT_F32 || (K->prec == QTT_F64 && f->prec == QTT_F64), "qtt_solve: FP64 solve needs FP64 K, f");
+  if (o.precision == QTT_F32) {
     Tptr Kc = own(nullptr), fc = own(nullptr);
     const qtt_tensor* Ku = K;
     const qtt_tensor* fu = f;
-    if (K->prec != prec) { Kc = own(tensor_clone(K, prec, s)); Ku = Kc.get(); }
-    if (f->prec != prec) { fc = own(tensor_clone(f, prec, s)); fu = fc.get(); }
-    Tptr x = x0 ? own(tensor_clone(x0, prec, s)) : default_x0(s, f, prec);
-    Tptr z = z0 ? own(tensor_clone(z0, prec, s)) : default_z0(s, f, rho, prec);
-    rc = prec == QTT_F64 ? amen_run<double>(s, Ku, fu, x.get(), z.get(), o.tol, o, inf)
-                         : amen_run<float>(s, Ku, fu, x.get(), z.get(), o.tol, o, inf);
-    if (prec == QTT_F64) {
-      // a passing in-sweep check stops the sweeps at once, so a stored value
-      // <= tol is the final iterate's residual; otherwise measure it now
-      if (!(inf->rel_residual > 0 && inf->rel_residual <= o.tol)) inf->rel_residual = residual64(s, K, x.get(), f);
-    }
+    if (K->prec != QTT_F32) { Kc = own(tensor_clone(K, QTT_F32, s)); Ku = Kc.get(); }
+    if (f->prec != QTT_F32) { fc = own(tensor_clone(f, QTT_F32, s)); fu = fc.get(); }
+    Tptr x = x0 ? own(tensor_clone(x0, QTT_F32, s)) : default_x0(s, f, QTT_F32);
+    Tptr z = z0 ? own(tensor_clone(z0, QTT_F32, s)) : default_z0(s, f, rho, QTT_F32);
+    rc = amen_run<float>(s, Ku, fu, x.get(), z.get(), o.tol, o, inf);
     *xout = x.release();
   } else {
-    QTT_REQUIRE(o.precision == QTT_MIXED, "qtt_solve: unknown precision");
-    QTT_REQUIRE(K->prec == QTT_F64 && f->prec == QTT_F64, "qtt_solve: mixed precision needs FP64 K and f");
-    // Sweeps with FP64 interfaces and local residuals; the Krylov cycles of
-    // every local solve apply an FP32 copy of the local operator (local
-    // iterative refinement).  Then the FP64 global residual r = f - K u
-    // (QTT matvec and sum in FP64) decides; if it is above tol, r is rounded
-    // in FP64, K d = r is solved the same way and u <- round64(u + d).
+    QTT_REQUIRE(o.precision == QTT_F64 || o.precision == QTT_MIXED, "qtt_solve: unknown precision");
+    QTT_REQUIRE(K->prec == QTT_F64 && f->prec == QTT_F64, "qtt_solve: FP64 and mixed solves need FP64 K and f");
+    // Sweeps with FP64 interfaces and local residuals; with QTT_MIXED the
+    // Krylov cycles of every local solve apply an FP32 copy of the local
+    // operator (local iterative refinement).  The FP64 global residual
+    // r = f - K u (QTT matvec in FP64) decides.  When the sweeps stall above
+    // tol, r is rounded in FP64 (randomized, round_residual_rand), K d = r is
+    // solved the same way to the inner tolerance, and u <- round64(u + d).
+    const bool mixed = o.precision == QTT_MIXED;
     const double inner = o.inner_tol > 0 ? o.inner_tol : 1e-3;
     const int refine_max = o.refine_max > 0 ? o.refine_max : (o.refine_max < 0 ? 0 : 4);
     Tptr u = x0 ? own(tensor_clone(x0, QTT_F64, s)) : default_x0(s, f, QTT_F64);
     Tptr z = z0 ? own(tensor_clone(z0, QTT_F64, s)) : default_z0(s, f, rho, QTT_F64);
-    rc = amen_run<double>(s, K, f, u.get(), z.get(), o.tol, o, inf, true);
+    rc = amen_run<double>(s, K, f, u.get(), z.get(), o.tol, o, inf, mixed, refine_max > 0);
+    double fnorm = -1.0;
     for (int it = 0;; ++it) {
-      Tptr r = own(nullptr);
-      const double rel = (it == 0 && inf->rel_residual > 0 && inf->rel_residual <= o.tol)
+      // a passing in-sweep check stops the sweeps at once, so a stored value
+      // <= tol is the final iterate's residual; otherwise measure it now
+      const double rel = (it == 0 && rc == QTT_OK && inf->rel_residual > 0 && inf->rel_residual <= o.tol)
                              ? inf->rel_residual
                              : residual64(s, K, u.get(), f);
       inf->rel_residual = rel;
-      if (o.verbose) fprintf(stderr, "[qtt_solve mixed] check %d: FP64 rel residual %.3e\n", it, rel);
+      if (o.verbose) fprintf(stderr, "[qtt_solve] check %d: FP64 rel residual %.3e\n", it, rel);
       if (rel <= o.tol || it >= refine_max) {
         rc = rel <= o.tol ? QTT_OK : QTT_ENOCONV;
         break;
       }
-      {
-        // r = f - K u by the FP64 QTT matvec, rounded in FP64
+      if (fnorm < 0) {
         Arena ar(s);
-        auto Ku = own(product<double>(s, K, u.get()));
-        r = own(tt_sum<double>(s, 1.0, f, -1.0, Ku.get()));
+        fnorm = norm<double>(s, ar, f);
+      }
+      int mr = 1;
+      for (int k = 0; k <= u->d; ++k) mr = std::max(mr, u->r[k]);
+      const int ell = std::min(512, std::max(64, 4 * mr + 16));
+      double kept = 0.0;
+      Tptr r = own(round_residual_rand(s, K, u.get(), f, ell, 0x5eed0000ULL + (unsigned long long)it, &kept));
+      if (o.verbose) {
+        const double full = rel * fnorm, frac = full > 0 ? kept / full : 1.0;
+        fprintf(stderr, "[qtt_solve] refinement %d: residual sketched at rank %d, relative error %.2e\n", it + 1, ell,
+                std::sqrt(std::max(0.0, 1.0 - frac * frac)));
+      }
+      {
+        Arena ar(s);
         round_tt<double>(s, ar, r.get(), std::min(1e-2, inner), 0);
       }
+      // the correction is noise-like and of higher rank than u: enrich twice as fast
       auto d = default_x0(s, f, QTT_F64);
-      auto zd = default_z0(s, f, rho, QTT_F64);
-      amen_run<double>(s, K, r.get(), d.get(), zd.get(), inner, o, inf, true);
+      auto zd = default_z0(s, f, 2 * rho, QTT_F64);
+      amen_run<double>(s, K, r.get(), d.get(), zd.get(), inner, o, inf, mixed, true, 0.0);
+      // u + d is rounded only at the level of FP64 noise: K amplifies the
+      // high-frequency part of a truncation error by up to its condition
+      // number (~4^L), so truncating u + d at anything near tol would
+      // undo the correction
       u = own(tt_sum<double>(s, 1.0, u.get(), 1.0, d.get()));
       Arena ar(s);
-      round_tt<double>(s, ar, u.get(), std::max(1e-15, 1e-3 * o.tol), o.max_rank > 0 ? o.max_rank : 0);
+      round_tt<double>(s, ar, u.get(), 1e-14, o.max_rank > 0 ? o.max_rank : 0);
       inf->refinements += 1;
     }
     *xout = u.release();

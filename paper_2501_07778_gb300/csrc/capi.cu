@@ -11,6 +11,7 @@ namespace qtt {
 namespace {
 thread_local std::string g_last_error;
 }
+double residual64(cudaStream_t s, const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* f);
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 }  // namespace qtt
 
@@ -178,23 +179,23 @@ int qtt_residual(const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* f, 
   QTT_API_BEGIN
   QTT_REQUIRE(K && u && f && out, "qtt_residual: null argument");
   QTT_REQUIRE(K->prec == QTT_F64 && u->prec == QTT_F64 && f->prec == QTT_F64, "qtt_residual: operands must be FP64");
+  QTT_REQUIRE(K->is_matrix && !u->is_matrix && !f->is_matrix && K->d == u->d && K->d == f->d,
+              "qtt_residual: K must be an MPO and u, f MPS of equal length");
   cudaStream_t s = as_stream(stream);
   StreamScope scope_(s);
-  Arena ar(s);
-  qtt_tensor* Ku = product<double>(s, K, u);
-  qtt_tensor* r = nullptr;
-  try {
-    r = tt_sum<double>(s, 1.0, f, -1.0, Ku);
-    double rn = norm<double>(s, ar, r);
-    double fn = norm<double>(s, ar, f);
-    *out = fn > 0 ? rn / fn : rn;
-  } catch (...) {
-    tensor_free(Ku);
-    tensor_free(r);
-    throw;
-  }
-  tensor_free(Ku);
-  tensor_free(r);
+  *out = residual64(s, K, u, f);
+  return QTT_OK;
+  QTT_API_END
+}
+
+int qtt_round_residual(const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* f, int rank,
+                       unsigned long long seed, double* kept_norm, qtt_tensor** r, void* stream) {
+  QTT_API_BEGIN
+  QTT_REQUIRE(K && u && f && r, "qtt_round_residual: null argument");
+  QTT_REQUIRE(K->d >= 2, "qtt_round_residual: needs at least two cores");
+  cudaStream_t s = as_stream(stream);
+  StreamScope scope_(s);
+  *r = round_residual_rand(s, K, u, f, rank, seed, kept_norm);
   return QTT_OK;
   QTT_API_END
 }

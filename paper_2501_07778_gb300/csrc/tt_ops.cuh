@@ -38,6 +38,12 @@ int truncation_rank(const std::vector<double>& sv, double delta, int max_rank, b
 template <typename T>
 int round_tt(cudaStream_t s, Arena& ar, qtt_tensor* x, double tol, int max_rank);
 
+// FP64 rank-ell approximation of f - K u by randomize-then-orthogonalize
+// rounding of the structured sum (new tensor, left-orthonormal cores);
+// *kept_norm = its norm.  The product cores of K u are never formed.
+qtt_tensor* round_residual_rand(cudaStream_t s, const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* f,
+                                int ell, unsigned long long seed, double* kept_norm);
+
 // B = A diag(S)
 template <typename T>
 void scale_columns(cudaStream_t s, int rows, int cols, const T* A, int lda, const T* S, T* B, int ldb);

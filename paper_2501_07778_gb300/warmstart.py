@@ -43,7 +43,7 @@ def _p(t):
 class WarmStartMLP:
     """4 -> H -> H -> P MLP (tanh) predicting rank-r cores for `modes`."""
 
-    def __init__(self, modes: Sequence[int], r: int = 16, H: int = 256, seed: int = 0, out_scale: float = 0.05):
+    def __init__(self, modes: Sequence[int], r: int = 16, H: int = 256, seed: int = 0, out_scale: float = 0.25):
         import torch
         self.modes = list(modes)
         self.r = r
@@ -62,6 +62,10 @@ class WarmStartMLP:
             "W3": (torch.randn(H, self.P, generator=g) * (out_scale / math.sqrt(H))).to(dev),
             "b3": torch.zeros(self.P, device=dev),
         }
+        # targets are learned divided by this norm scale (set by train), so
+        # that the predicted TT starts at a norm comparable to the targets':
+        # with a scale far off, a product of D cores and its gradients vanish
+        self.target_scale = 1.0
         self.m = {k: torch.zeros_like(v) for k, v in self.params.items()}
         self.v = {k: torch.zeros_like(v) for k, v in self.params.items()}
         self.t = 0
@@ -140,7 +144,7 @@ class WarmStartMLP:
         modes = (C.c_int * len(self.modes))(*self.modes)
         for b in range(params.shape[0]):
             h = C.c_void_p()
-            scale = float(params[b, 2] / params[b, 0])
+            scale = float(params[b, 2] / params[b, 0]) * self.target_scale
             _check(lib().qtt_ws_to_tensor(C.c_void_p(out[b].data_ptr()), len(self.modes), modes, self.r, scale,
                                           C.byref(h), _stream(None)), "qtt_ws_to_tensor")
             xs.append(QTT(h))
@@ -175,8 +179,11 @@ def dataset(seed: int, count: int, nus: Sequence[float]):
 def train(net: WarmStartMLP, basis: List[QTT], P: np.ndarray, coef: np.ndarray, steps: int = 300, batch: int = 32,
           lr: float = 2e-3, seed: int = 0):
     """Adam on random mini-batches; the learning rate decays by 10x over the
-    run.  Returns the per-step mean losses."""
+    run.  Targets are divided by the RMS norm of the basis solutions (the
+    network's target_scale).  Returns the per-step mean (relative) losses."""
     gram = net.basis_gram(basis)
+    net.target_scale = float(np.sqrt(np.mean(np.diag(gram))))
+    coef = np.asarray(coef) / net.target_scale
     rng = np.random.default_rng(seed)
     losses = []
     for st in range(steps):

@@ -89,3 +89,60 @@ def test_batched_uneven_problems_match_oracle():
         ug = q.qtt_to_full(u).cpu().numpy()
         ref = fem.solve_duplicated(p)
         assert np.linalg.norm(ug - ref) / np.linalg.norm(ref) <= 1e-8
+
+
+def _oracle_residual(prob, u_cores):
+    Ko, fo = assembly.assemble(prob)
+    return tt.full(fo) - tt.full_matrix(Ko) @ tt.full(u_cores)
+
+
+def test_round_residual_full_rank_is_exact():
+    """At a sketch rank that reaches the ranks of f - K u, the randomized
+    rounding returns the residual itself (oracle: dense f - K u)."""
+    prob = W.plate_body_force(3)
+    K, f = q.qtt_assemble_stiffness(prob)
+    uc = W.random_tt(21, W.qtt_modes(prob), [1, 3, 5, 4, 1])
+    r, kept = q.qtt_round_residual(K, q.QTT.from_cores(uc), f, rank=512, seed=3)
+    ro = _oracle_residual(prob, uc)
+    rg = q.qtt_to_full(r).cpu().numpy()
+    assert np.linalg.norm(rg - ro) <= 1e-11 * np.linalg.norm(ro)
+    assert abs(kept - np.linalg.norm(ro)) <= 1e-11 * np.linalg.norm(ro)
+
+
+@pytest.mark.parametrize("rank", [4, 12, 40])
+def test_round_residual_is_orthogonal_projection(rank):
+    """||r - r~||^2 + ||r~||^2 = ||r||^2 at any sketch rank, the error shrinks
+    as the rank grows, and the cores come back left-orthonormal."""
+    prob = W.plate_traction_smooth(5)
+    K, f = q.qtt_assemble_stiffness(prob)
+    uc = W.random_tt(22, W.qtt_modes(prob), [1, 4, 6, 6, 6, 4, 1])
+    r, kept = q.qtt_round_residual(K, q.QTT.from_cores(uc), f, rank=rank, seed=7)
+    ro = _oracle_residual(prob, uc)
+    rg = q.qtt_to_full(r).cpu().numpy()
+    nr, ne = np.linalg.norm(ro), np.linalg.norm(ro - rg)
+    assert abs(kept - np.linalg.norm(rg)) <= 1e-12 * nr
+    assert abs(ne ** 2 + kept ** 2 - nr ** 2) <= 1e-10 * nr ** 2
+    cores = r.cores()
+    for c in cores[:-1]:
+        m = c.reshape(-1, c.shape[-1], order="F")
+        np.testing.assert_allclose(m.T @ m, np.eye(m.shape[1]), atol=1e-12)
+    if rank == 40:
+        # the sketch reaches at least the TT-SVD of the same rank within a small factor
+        best = tt.tt_svd(ro, W.qtt_modes(prob), 0.0, max_rank=rank)
+        assert ne <= 5.0 * np.linalg.norm(ro - tt.full(best)) + 1e-12 * nr
+
+
+@pytest.mark.parametrize("precision", [q.QTT_F64, q.QTT_MIXED])
+def test_refinement_recovers_truncated_sweeps(precision):
+    """Sweeps cut short (five sweeps, slow rank growth) leave the first
+    iterate far above tol; the outer refinement (randomized FP64 residual,
+    correction solve, u + d) must still reach the sparse direct solution."""
+    prob = W.plate_body_force(5)
+    K, f = q.qtt_assemble_stiffness(prob)
+    u, info = q.qtt_solve(K, f, tol=1e-9, precision=precision, kick_rank=4, max_sweeps=5, refine_max=12)
+    ug = q.qtt_to_full(u).cpu().numpy()
+    ref = fem.solve_duplicated(prob)
+    err = np.linalg.norm(ug - ref) / np.linalg.norm(ref)
+    assert info["refinements"] >= 1, info
+    assert info["rc"] == 0 and info["rel_residual"] <= 1e-9, info
+    assert err <= 1e-7, (err, info)
