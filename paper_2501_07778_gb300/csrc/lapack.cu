@@ -22,6 +22,11 @@ __device__ __forceinline__ double wsum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+__device__ __forceinline__ float wsum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 
 template <typename T>
 __device__ double block_sum(double v, double* red) {
@@ -133,14 +138,14 @@ inline int grid_for(long long n) { return (int)std::max<long long>(1, std::min<l
 // ---------------------------------------------------------------------------
 // One-sided Jacobi on W (m x n, ldw) accumulating V (n x n, ldv); single CTA.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, typename Acc = double>
 __global__ void __launch_bounds__(1024) jacobi_kernel(int m, int n, T* W, int ldw, T* Vm, int ldv, int max_sweeps,
                                                       int* sweeps_out) {
   __shared__ int rotated;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int np = n + (n & 1);                  // even number of positions
-  const double tol = 1e-15 * (double)(m > 1 ? m : 1);
-  const double tolf = (sizeof(T) == 4) ? 1e-7 * (double)(m > 1 ? m : 1) : tol;
+  const Acc tol = (Acc)(1e-15 * (double)(m > 1 ? m : 1));
+  const Acc tolf = (sizeof(T) == 4) ? (Acc)(1e-7 * (double)(m > 1 ? m : 1)) : tol;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     if (threadIdx.x == 0) rotated = 0;
@@ -160,9 +165,9 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int m, int n, T* W, int ld
         if (q >= n) continue;                  // dummy position for odd n
         T* wp = W + (long long)p * ldw;
         T* wq = W + (long long)q * ldw;
-        double al = 0.0, be = 0.0, ga = 0.0;
+        Acc al = 0, be = 0, ga = 0;
         for (int i = lane; i < m; i += 32) {
-          double a = wp[i], b = wq[i];
+          Acc a = wp[i], b = wq[i];
           al += a * a;
           be += b * b;
           ga += a * b;
@@ -170,19 +175,19 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int m, int n, T* W, int ld
         al = wsum(al);
         be = wsum(be);
         ga = wsum(ga);
-        if (ga == 0.0 || !(fabs(ga) > tolf * sqrt(al * be))) continue;
-        double zeta = (be - al) / (2.0 * ga);
-        double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+        if (ga == (Acc)0 || !(fabs(ga) > tolf * sqrt(al * be))) continue;
+        Acc zeta = (be - al) / ((Acc)2 * ga);
+        Acc t = (zeta >= (Acc)0 ? (Acc)1 : (Acc)-1) / (fabs(zeta) + sqrt((Acc)1 + zeta * zeta));
+        Acc cs = (Acc)1 / sqrt((Acc)1 + t * t), sn = cs * t;
         for (int i = lane; i < m; i += 32) {
-          double a = wp[i], b = wq[i];
+          Acc a = wp[i], b = wq[i];
           wp[i] = (T)(cs * a - sn * b);
           wq[i] = (T)(sn * a + cs * b);
         }
         T* vp = Vm + (long long)p * ldv;
         T* vq = Vm + (long long)q * ldv;
         for (int i = lane; i < n; i += 32) {
-          double a = vp[i], b = vq[i];
+          Acc a = vp[i], b = vq[i];
           vp[i] = (T)(cs * a - sn * b);
           vq[i] = (T)(sn * a + cs * b);
         }
@@ -421,11 +426,52 @@ void svd(cudaStream_t s, Arena& ar, int m, int n, T* A, int lda, T* U, int ldu, 
   T* Vm = ar.alloc<T>((size_t)n * n);
   set_identity_kernel<T><<<grid_for((long long)n * n), 256, 0, s>>>(Vm, n, n, n);
   QTT_CHECK_LAUNCH();
-  ProfToken pj = prof_begin(PROF_JACOBI, s);
-  jacobi_kernel<T><<<1, 1024, 0, s>>>(k, n, R, k, Vm, n, 40, nullptr);
-  QTT_CHECK_LAUNCH();
-  // nominal work of one sweep over all pairs (the sweep count is data dependent)
-  if (pj.ev) prof_end(pj, s, 0.5 * n * (n - 1) * (6.0 * k + 12.0 * k + 12.0 * n), sizeof(T) * 2.0 * (k + n) * n);
+  if (sizeof(T) == 8 && n >= 24) {
+    // Mixed-precision preconditioning (one CTA runs the Jacobi sweeps, and
+    // one SM has 1/64 of its FP32 rate in FP64): the sweeps run first in
+    // FP32 on an FP32 copy of R, their rotations V32 are made orthogonal to
+    // FP64 accuracy by two Newton-Schulz steps V <- V (3 I - V^T V) / 2, and
+    // R <- R V.  The FP64 sweeps below then start from nearly orthogonal
+    // columns and converge (quadratically) in a sweep or two.
+    float* R32 = ar.alloc<float>((size_t)k * n);
+    float* V32 = ar.alloc<float>((size_t)n * n);
+    convert<T, float>(s, R, R32, (size_t)k * n);
+    set_identity_kernel<float><<<grid_for((long long)n * n), 256, 0, s>>>(V32, n, n, n);
+    QTT_CHECK_LAUNCH();
+    ProfToken pf = prof_begin(PROF_JACOBI, s);
+    jacobi_kernel<float, float><<<1, 1024, 0, s>>>(k, n, R32, k, V32, n, 40, nullptr);
+    QTT_CHECK_LAUNCH();
+    if (pf.ev) prof_end(pf, s, 0.5 * n * (n - 1) * (6.0 * k + 12.0 * k + 12.0 * n), 4.0 * 2.0 * (k + n) * n);
+    T* V0 = ar.alloc<T>((size_t)n * n);
+    T* X = ar.alloc<T>((size_t)n * n);
+    T* V1 = ar.alloc<T>((size_t)n * n);
+    convert<float, T>(s, V32, V0, (size_t)n * n);
+    for (int it = 0; it < 2; ++it) {
+      gemm<T>(s, true, false, n, n, n, T(1), V0, n, 0, V0, n, 0, T(0), X, n, 0);        // X = V^T V
+      QTT_CUDA(cudaMemcpyAsync(V1, V0, sizeof(T) * n * n, cudaMemcpyDeviceToDevice, s));
+      gemm<T>(s, false, false, n, n, n, T(-0.5), V0, n, 0, X, n, 0, T(1.5), V1, n, 0);   // V1 = 1.5 V - 0.5 V X
+      std::swap(V0, V1);
+    }
+    T* W = ar.alloc<T>((size_t)k * n);
+    gemm<T>(s, false, false, k, n, n, T(1), R, k, 0, V0, n, 0, T(0), W, k, 0);           // W = R V
+    QTT_CUDA(cudaMemcpyAsync(R, W, sizeof(T) * k * n, cudaMemcpyDeviceToDevice, s));
+    QTT_CUDA(cudaMemcpyAsync(Vm, V0, sizeof(T) * n * n, cudaMemcpyDeviceToDevice, s));
+    // the FP64 sweeps accumulate their rotations in V2; Vm <- Vm V2 afterwards
+    T* V2 = ar.alloc<T>((size_t)n * n);
+    set_identity_kernel<T><<<grid_for((long long)n * n), 256, 0, s>>>(V2, n, n, n);
+    QTT_CHECK_LAUNCH();
+    ProfToken pj = prof_begin(PROF_JACOBI, s);
+    jacobi_kernel<T><<<1, 1024, 0, s>>>(k, n, R, k, V2, n, 40, nullptr);
+    QTT_CHECK_LAUNCH();
+    if (pj.ev) prof_end(pj, s, 0.5 * n * (n - 1) * (6.0 * k + 12.0 * k + 12.0 * n), sizeof(T) * 2.0 * (k + n) * n);
+    gemm<T>(s, false, false, n, n, n, T(1), V0, n, 0, V2, n, 0, T(0), Vm, n, 0);
+  } else {
+    ProfToken pj = prof_begin(PROF_JACOBI, s);
+    jacobi_kernel<T><<<1, 1024, 0, s>>>(k, n, R, k, Vm, n, 40, nullptr);
+    QTT_CHECK_LAUNCH();
+    // nominal work of one sweep over all pairs (the sweep count is data dependent)
+    if (pj.ev) prof_end(pj, s, 0.5 * n * (n - 1) * (6.0 * k + 12.0 * k + 12.0 * n), sizeof(T) * 2.0 * (k + n) * n);
+  }
   int* order = ar.alloc<int>(n);
   svd_finish_kernel<T><<<1, 1024, sizeof(double) * n, s>>>(k, n, R, k, S, order);
   QTT_CHECK_LAUNCH();
