@@ -9,10 +9,11 @@ solve when its FP64 relative residual ||f - K u|| / ||f|| (exact QTT matvec
 and sum in FP64, normed in full format) is <= 1e-8.  value = accepted solves
 per second over all ranks (max-over-ranks time).
 
---form fast   (default) learned warm start (MLP inference, trained once per
-              run outside the timed region on superpositions of method
-              solves) + mixed precision (FP64 interfaces and residuals, FP32
-              Krylov operators, FP64 refinement) + batched concurrent solves
+--form fast   (default) mixed precision (FP64 interfaces and residuals, FP32
+              Krylov operators, FP64 outer refinement) + batched concurrent
+              solves; with --warm-start also the learned warm start (MLP
+              inference, trained once per run outside the timed region on
+              superpositions of method solves)
 --form plain  FP64 AMEn, cold start, one solve at a time
 --impl reference   the oracle (NumPy/SciPy FP64 on the host cores) on bounded
                    samples of the same workload
@@ -134,6 +135,21 @@ def workload(L: int, count: int, rank: int, world: int, seed: int = 2):
     P = W.plate_params(seed, count * world)[rank::world]
     probs = [W.plate_top_traction(L, float(E), float(nu), float(a), float(t)) for E, nu, a, t in P]
     return np.asarray(P), probs
+
+
+def combine_ranks(ms: float, accepted: int, total: int, dist=None, device: str = "cpu"):
+    """Whole-job numbers over all ranks: the slowest rank's timed milliseconds
+    and the sums of accepted and attempted solves; value = accepted solves
+    per second of that time.  Returns (ms, accepted, total, value)."""
+    import torch
+    t_ms = torch.tensor([ms], dtype=torch.float64, device=device)
+    t_n = torch.tensor([float(accepted), float(total)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t_ms, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t_n, op=dist.ReduceOp.SUM)
+    ms_all, acc_all, tot_all = float(t_ms[0]), float(t_n[0]), float(t_n[1])
+    value = acc_all / (ms_all / 1e3) if ms_all > 0 else 0.0
+    return ms_all, acc_all, tot_all, value
 
 
 def solve_kw(form: str, tol: float):
@@ -373,14 +389,7 @@ def main():
     barrier()
     launches = lib.qtt_kernel_launches() - launches0
     clocks = sampler.stop()
-    t = torch.tensor([ms, float(accepted), float(total)], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(tmax[1:], op=dist.ReduceOp.SUM)
-        t = tmax
-    ms_all, acc_all, tot_all = float(t[0]), float(t[1]), float(t[2])
-    value = acc_all / (ms_all / 1e3) if ms_all > 0 else 0.0
+    ms_all, acc_all, tot_all, value = combine_ranks(ms, accepted, total, dist, device="cuda")
 
     # ---- dominant kernel class: one extra step with CUDA events per launch
     log(f"timed: {ms_all:.1f} ms for {tot_all:.0f} solves ({acc_all:.0f} accepted)")
