@@ -4,16 +4,20 @@
 //   right-orthogonalise x and the residual proxy z; build right interfaces
 //   Phi_R(x,K,x), Psi_R(x,f), Phi_R(z,K,x), Psi_R(z,f);
 //   for k = 1..D: local Galerkin system B_k = Phi_L K_k Phi_R, local rhs g_k;
-//     record ||B_k x_k - g_k|| / ||g_k||; solve (dense LU or restarted
-//     GMRES); truncate the left unfolding by SVD at the smallest rank whose
-//     local residual stays within tol / sqrt(D); new z core = orth of the
+//     record ||B_k x_k - g_k|| / ||g_k||; solve (dense LU, Jacobi-
+//     preconditioned CG for a symmetric K, restarted GMRES otherwise);
+//     truncate the left unfolding by SVD at the smallest rank whose local
+//     residual stays within tol / sqrt(D); new z core = orth of the
 //     residual projected on z's interfaces; enrich [U, residual projected on
 //     x's left and z's right interfaces], orthogonalise, push the remainder
 //     into core k+1; update the left interfaces;
-//   stop when the sweep's largest local residual is <= tol.
-// Mixed precision (QTT_MIXED): the sweeps run in FP32 and the outer loop
-// forms r = f - K u by the QTT matvec in FP64, rounds it in FP64, solves
-// K d = r in FP32 and updates u <- round64(u + d).
+//   stop when the sweep's largest local residual is <= tol, or (FP64
+//   interfaces) when the FP64 global residual is <= tol.
+// QTT_F64 and QTT_MIXED keep interfaces and residuals in FP64; QTT_MIXED
+// runs the local Krylov iterations on an FP32 copy of the local operator.
+// When the sweeps stall above tol, both refine: r = f - K u rounded in FP64
+// by randomized TT rounding (residual.cu), K d = r solved the same way to a
+// looser tolerance, u <- u + d.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -1035,7 +1039,8 @@ int solve(const qtt_tensor* K, const qtt_tensor* f, const qtt_tensor* x0, const 
     // operator (local iterative refinement).  The FP64 global residual
     // r = f - K u (QTT matvec in FP64) decides.  When the sweeps stall above
     // tol, r is rounded in FP64 (randomized, round_residual_rand), K d = r is
-    // solved the same way to the inner tolerance, and u <- round64(u + d).
+    // solved the same way to the inner tolerance, and u <- u + d (rounded at
+    // the level of FP64 noise only).
     const bool mixed = o.precision == QTT_MIXED;
     const double inner = o.inner_tol > 0 ? o.inner_tol : 1e-3;
     const int refine_max = o.refine_max > 0 ? o.refine_max : (o.refine_max < 0 ? 0 : 4);
