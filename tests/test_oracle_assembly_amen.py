@@ -93,3 +93,25 @@ def test_amen_local_helpers_match_dense():
     v = np.random.default_rng(0).standard_normal((r1, n, r2))
     np.testing.assert_allclose(amen.local_apply(PhiL, K[1], PhiR, v).reshape(-1, order="F"),
                                B @ v.reshape(-1, order="F"), atol=1e-10 * np.abs(Kd).max())
+
+
+@pytest.mark.parametrize("make,L", [(W.plate_body_force, 7), (W.lshape_shear, 6)])
+def test_transpose_identity_at_large_level(make, L):
+    """<K x, y> = <x, K^T y> in QTT arithmetic at levels too large for dense
+    checks (a transposed operand or swapped mode pair in the matvec or the
+    MPO transpose breaks it for the non-symmetric multi-patch K); for one
+    patch K is symmetric, so <K x, y> = <x, K y> as well."""
+    prob = make(L)
+    K, _ = assembly.assemble(prob)
+    modes = W.qtt_modes(prob)
+    x = W.random_tt(31, modes, [1] + [3] * (len(modes) - 1) + [1])
+    y = W.random_tt(32, modes, [1] + [4] * (len(modes) - 1) + [1])
+    lhs = tt.dot(tt.matvec(K, x), y)
+    rhs = tt.dot(x, tt.matvec(tt.transpose_mpo(K), y))
+    scale = tt.norm(tt.matvec(K, x)) * tt.norm(y)
+    assert abs(lhs - rhs) <= 1e-12 * scale
+    if prob.q == 1:
+        assert abs(lhs - tt.dot(x, tt.matvec(K, y))) <= 1e-12 * scale
+    else:
+        # the concatenated system is not symmetric: the identity is not trivial
+        assert abs(lhs - tt.dot(x, tt.matvec(K, y))) > 1e-8 * scale
