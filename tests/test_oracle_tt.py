@@ -3,6 +3,7 @@ inputs, textbook QTT ranks of elementary functions, the rounding error bound
 of Oseledets (2011), and the recursive (quadrant) definition of Morton
 order."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -186,6 +187,12 @@ def test_erank_and_parameter_counts():
     prints for d = 2 in its N_d-versus-d plots (Section 5.3)."""
     x = W.random_tt(1, [4, 4, 4, 2], [1, 5, 5, 5, 1])
     assert tt.erank(x) == pytest.approx(5.0)
-    y = W.random_tt(2, [4, 4, 2], [1, 4, 2, 1])
-    assert tt.n_params(y) == 52
+    golden = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_Nd_d2.txt")
+    rows = [ln.split() for ln in open(golden) if ln.strip() and not ln.startswith("#")]
+    d, nd, modes, ranks = rows[0]
+    modes = [int(v) for v in modes.split(",")]
+    ranks = [int(v) for v in ranks.split(",")]
+    assert int(d) == 2 and len(modes) == int(d) + 1
+    y = W.random_tt(2, modes, ranks)
+    assert tt.n_params(y) == int(nd)
     assert tt.max_rank(y) == 4
