@@ -1,22 +1,33 @@
 #!/usr/bin/env python
 """Benchmark: QTT solves/sec at relative residual 1e-8 on L = 12 plates.
 
-One step = the whole hot path over one batch of synthetic problems of the
-square-plate family (left edge clamped, constant traction of amplitude amp at
-angle theta on the top edge, n = 2^12 nodes per side, 33.5 M DOFs): assemble
-K and f on the device (Algorithm 1), solve K u = f with AMEn, and accept the
-solve when its FP64 relative residual ||f - K u|| / ||f|| (exact QTT matvec
-and sum in FP64, normed in full format) is <= 1e-8.  value = accepted solves
-per second over all ranks (max-over-ranks time).
+One step = the whole hot path for one synthetic problem of the square-plate
+family (left edge clamped, constant traction of amplitude amp at angle theta
+on the top edge, n = 2^12 nodes per side, 33.5 M DOFs): assemble K and f on
+the device from the host problem description (Algorithm 1), solve K u = f
+with AMEn, and accept the solve when its FP64 relative residual
+||f - K u|| / ||f|| (exact QTT matvec and sum in FP64, normed in full
+format) is <= 1e-8.  value = accepted solves per second of CUDA-event time
+over the timed steps (max over ranks).
 
---form fast   (default) mixed precision (FP64 interfaces and residuals, FP32
-              Krylov operators, FP64 outer refinement) + batched concurrent
-              solves; with --warm-start also the learned warm start (MLP
-              inference, trained once per run outside the timed region on
-              superpositions of method solves)
---form plain  FP64 AMEn, cold start, one solve at a time
---impl reference   the oracle (NumPy/SciPy FP64 on the host cores) on bounded
-                   samples of the same workload
+Every timed step also gives the end-to-end figure: host wall time from the
+host problem description to the solution cores and the solve record read
+back into host memory (the e2e object), measured in the same loop.
+
+Forms:
+  --form fast   (default) mixed precision: FP64 interfaces and residuals,
+                FP32 Krylov operators, FP64 outer refinement; with
+                --warm-start also the learned warm start (MLP inference;
+                the network is trained before the timed region)
+  --form plain  FP64 AMEn, cold start, one solve at a time
+The fast-form line also carries a `plain` object: the plain form timed on
+the first `--plain-solves` problems of the same workload after the timed
+steps (the comparison the metric names).
+
+--impl reference   the oracle (NumPy/SciPy FP64 on the host cores): each
+                   step one complete oracle solve of a plate problem of the
+                   same family at level --ref-L (an L = 12 oracle solve takes
+                   minutes; the level is named in the line)
 
 Multi-GPU: problems are independent; rank r solves every world-th problem
 (weak scaling, no data-path collective; a barrier and a max reduction of the
@@ -26,7 +37,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -41,34 +51,42 @@ METRIC = "QTT solves/sec at rel. residual 1e-8 (L=12); fast form vs plain FP64 G
 ACCEPT = 1e-8
 MAX_SWEEPS = 24
 _T0 = time.perf_counter()
+CLASSES = {0: "gemm_f64", 1: "gemm_f32", 2: "core_product", 3: "qr_panel", 4: "jacobi_svd", 5: "lu_panel",
+           6: "permute", 7: "to_full", 8: "pcg_f32"}
 
 
 def log(msg: str):
     print(f"[bench {time.perf_counter() - _T0:8.1f}s] {msg}", file=sys.stderr, flush=True)
+
+
 NU_GRID = (0.2, 0.283, 0.367, 0.45)
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="fast", choices=["fast", "plain"])
-    ap.add_argument("--batch", type=int, default=0, help="problems per step per rank (0: 2 fast, 1 plain)")
-    ap.add_argument("--workers", type=int, default=2, help="concurrent solves in the batched form")
+    ap.add_argument("--batch", type=int, default=1, help="problems per step per rank")
+    ap.add_argument("--workers", type=int, default=1, help="concurrent solves when --batch > 1")
     ap.add_argument("--max-sweeps", type=int, default=24)
     ap.add_argument("--L", type=int, default=12)
     ap.add_argument("--tol", type=float, default=ACCEPT)
+    ap.add_argument("--plain-solves", type=int, default=1,
+                    help="fast form: plain FP64 solves timed after the timed steps (0: none)")
+    ap.add_argument("--plain-budget", type=float, default=1500.0,
+                    help="start no plain solve once the run has taken this many seconds")
     ap.add_argument("--train-steps", type=int, default=400)
     ap.add_argument("--warm-start", action="store_true",
-                    help="fast form with the learned warm start (8 basis solves + MLP training before timing); "
-                         "off by default: at L=12 the trained network does not yet beat a cold start")
-    ap.add_argument("--no-warm-start", action="store_true", help="(the default) fast form without the warm start")
+                    help="fast form with the learned warm start (8 basis solves + MLP training before timing)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle AMEn work per CPU sample")
-    return ap.parse_args()
+    ap.add_argument("--ref-L", type=int, default=6, help="level of the complete oracle solves (CPU legs)")
+    ap.add_argument("--cpu-solves", type=int, default=3, help="timed oracle solves of the cpu_baseline leg")
+    ap.add_argument("--no-profile", action="store_true",
+                    help="do not bracket the timed launches with the per-class CUDA-event profiler")
+    return ap.parse_args(argv)
 
 
 # ----------------------------------------------------------------------------
@@ -137,6 +155,11 @@ def workload(L: int, count: int, rank: int, world: int, seed: int = 2):
     return np.asarray(P), probs
 
 
+def workload_name(L: int) -> str:
+    return (f"plate L={L} ({2 * 4 ** L} DOFs), clamped left, constant top-edge traction; "
+            f"(E, nu, amp, angle) from the held-out seed-2 set")
+
+
 def combine_ranks(ms: float, accepted: int, total: int, dist=None, device: str = "cpu"):
     """Whole-job numbers over all ranks: the slowest rank's timed milliseconds
     and the sums of accepted and attempted solves; value = accepted solves
@@ -154,25 +177,37 @@ def combine_ranks(ms: float, accepted: int, total: int, dist=None, device: str =
 
 def solve_kw(form: str, tol: float):
     import paper_2501_07778_gb300 as q
-    if form == "plain":
-        return dict(tol=tol, precision=q.QTT_F64, kick_rank=8, max_sweeps=MAX_SWEEPS)
-    return dict(tol=tol, precision=q.QTT_MIXED, kick_rank=8, max_sweeps=MAX_SWEEPS)
+    prec = q.QTT_F64 if form == "plain" else q.QTT_MIXED
+    return dict(tol=tol, precision=prec, kick_rank=8, max_sweeps=MAX_SWEEPS)
+
+
+def problem_bytes(prob) -> int:
+    """Bytes of the host problem description the library reads (the C
+    struct and its arrays)."""
+    q = prob.q
+    return 2 * 4 + 2 * 8 + 2 * 8 + 2 * q * 4 + 4 * q * 4 + len(prob.body) * (3 * 4 + 8) + \
+        len(prob.traction) * (2 * 4 + 2 * 8)
 
 
 def run_step(form, params, probs, net, tol, workers):
-    """The hot path over one batch: assembly, (warm start), solve, FP64 check."""
+    """The hot path over one batch: assembly, (warm start), solve with the
+    FP64 residual check.  Returns (solutions, infos)."""
     import paper_2501_07778_gb300 as q
     KF = [q.qtt_assemble_stiffness(p) for p in probs]
+    x0s = net.predict(params) if (net is not None and form == "fast") else [None] * len(probs)
+    if len(probs) == 1:
+        u, i = q.qtt_solve(KF[0][0], KF[0][1], x0=x0s[0], check=False, **solve_kw(form, tol))
+        return [u], [i]
     if form == "plain":
         out = [q.qtt_solve(K, f, check=False, **solve_kw(form, tol)) for K, f in KF]
         return [u for u, _ in out], [i for _, i in out]
-    x0s = net.predict(params) if net is not None else None
-    return q.qtt_solve_batched([K for K, _ in KF], [f for _, f in KF], x0s, nworkers=workers, **solve_kw(form, tol))
+    return q.qtt_solve_batched([K for K, _ in KF], [f for _, f in KF], x0s, nworkers=workers,
+                               **solve_kw(form, tol))
 
 
 def train_warm_start(L: int, tol: float, steps: int):
-    """Method solves at the nu grid (batched), then the MLP on 2000
-    superposition targets.  Returns (net, info)."""
+    """Method solves at the nu grid, then the MLP on 2000 superposition
+    targets.  Returns (net, info)."""
     import workloads as W
     from paper_2501_07778_gb300 import QTT_F32, QTT_MIXED
     from paper_2501_07778_gb300 import warmstart as ws
@@ -185,13 +220,9 @@ def train_warm_start(L: int, tol: float, steps: int):
     modes = W.qtt_modes(W.plate_top_traction(L, 1.0, 0.3, 1.0, 0.0))
     net = ws.WarmStartMLP(modes, r=16, H=256, seed=0)
     P, coef = ws.dataset(1, 2000, NU_GRID)
-    # Adam at 3e-4 decaying 10x: 2e-3 diverges on the 13-core product, 1e-4
-    # barely moves in a few hundred steps
     losses = ws.train(net, basis, P, coef, steps=steps, batch=32, lr=3e-4)
     t2 = time.perf_counter()
     last = float(sum(losses[-10:]) / 10)
-    # a network no better than predicting zero (relative loss >= 1) would only
-    # slow the sweeps down: the solves then start cold
     used = last < 0.5
     return net if used else None, {"basis_solves": len(basis), "basis_s": round(t1 - t0, 2), "train_steps": steps,
                                    "train_s": round(t2 - t1, 2), "loss_first": round(float(losses[0]), 5),
@@ -199,66 +230,21 @@ def train_warm_start(L: int, tol: float, steps: int):
 
 
 # ----------------------------------------------------------------------------
-# CPU: the oracle on bounded samples
+# CPU: complete oracle solves
 # ----------------------------------------------------------------------------
-def oracle_sample(prob, tol: float, budget_s: float, sweeps_needed: int = None):
-    """Oracle (O-2 assembly + AMEn, NumPy FP64 on the host cores) on one
-    problem: the assembly is timed in full, the AMEn sweeps for at most
-    budget_s seconds; if the solve has not finished, the time per solve is
-    extrapolated from the measured time per sweep to sweeps_needed sweeps
-    (the sweep count of the GPU solve of the same problem)."""
+def oracle_solve(prob, tol: float):
+    """One complete oracle solve (O-2 assembly of K and f in QTT + AMEn to
+    tol, NumPy/SciPy FP64 on the host cores).  Returns (seconds, sweeps)."""
     import numpy as np
     import workloads as W
     from oracle import amen, assembly
     t0 = time.perf_counter()
     K, f = assembly.assemble(prob)
-    t_asm = time.perf_counter() - t0
     modes = W.qtt_modes(prob)
     x0 = [np.ones((1, n, 1)) for n in modes]
     z0 = W.random_tt(1, modes, [1] + [8] * (len(modes) - 1) + [1])
-    stamps = []
-    t1 = time.perf_counter()
-    deadline = t1 + budget_s
-
-    class Stop(Exception):
-        pass
-
-    def on_sweep(k, res):
-        stamps.append(time.perf_counter())
-        if stamps[-1] > deadline:
-            raise Stop()
-
-    orig = amen.local_apply
-
-    def bounded(*a, **k):
-        # a late sweep can take minutes in NumPy: stop inside it as well
-        if time.perf_counter() > deadline + 10.0 and stamps:
-            raise Stop()
-        return orig(*a, **k)
-
-    amen.local_apply = bounded
-    finished = True
-    try:
-        _, info = amen.amen_solve(K, f, x0, z0, tol, max_sweeps=40, local_direct_max=2048, on_sweep=on_sweep)
-        sweeps = info.sweeps
-    except Stop:
-        finished = False
-    finally:
-        amen.local_apply = orig
-    t_amen = time.perf_counter() - t1
-    if finished:
-        per = t_asm + t_amen
-        desc = f"oracle assembly + AMEn, one full L={prob.L} solve ({sweeps} sweeps, {per:.1f} s)"
-    else:
-        # completed sweeps timed; the remaining ones priced at the last
-        # (largest-rank) sweep's time -- a lower bound, ranks keep growing
-        need = max(sweeps_needed or 15, len(stamps))
-        last = stamps[-1] - (stamps[-2] if len(stamps) > 1 else t1)
-        per = t_asm + (stamps[-1] - t1) + last * (need - len(stamps))
-        desc = (f"oracle assembly of one L={prob.L} problem ({t_asm:.1f} s) + oracle AMEn for {len(stamps)} "
-                f"sweeps ({stamps[-1] - t1:.1f} s), the remaining {need - len(stamps)} of {need} sweeps (the GPU "
-                f"solve's count) priced at the last sweep's {last:.2f} s (lower bound)")
-    return per, desc
+    _, info = amen.amen_solve(K, f, x0, z0, tol, max_sweeps=40, local_direct_max=2048)
+    return time.perf_counter() - t0, info.sweeps
 
 
 def cpu_threads():
@@ -280,29 +266,53 @@ def cpu_model():
     return "unknown"
 
 
+def cpu_baseline(L: int, tol: float, solves: int):
+    """Median of `solves` complete oracle solves after one untimed warm-up
+    solve, on held-out problems of the plate family at level L."""
+    _, probs = workload(L, solves + 1, 0, 1)
+    oracle_solve(probs[0], tol)
+    times, sweeps = [], []
+    for p in probs[1:]:
+        t, s = oracle_solve(p, tol)
+        times.append(t)
+        sweeps.append(s)
+    med = statistics.median(times)
+    return {"value": 1.0 / med, "unit": "solves/s", "cores": cpu_threads(), "kind": "oracle",
+            "sample": (f"{solves} complete oracle solves (QTT assembly + AMEn to {tol:g}) of L={L} plates of the same "
+                       f"family, median {med:.2f} s after one warm-up solve (sweeps {sweeps}); an L=12 oracle solve "
+                       f"takes minutes per problem, beyond the run's budget"),
+            "L": L, "cpu": cpu_model()}
+
+
 # ----------------------------------------------------------------------------
 # reference arm: the oracle
 # ----------------------------------------------------------------------------
 def reference_main(args):
     if int(os.environ.get("RANK", "0")) != 0:
         return 0
-    P, probs = workload(args.L, args.warmup + args.steps, 0, 1)
-    times, desc = [], ""
-    for i in range(args.warmup + args.steps):
-        per, desc = oracle_sample(probs[i], args.tol, max(5.0, min(args.cpu_budget, 60.0)))
+    _, probs = workload(args.ref_L, args.warmup + args.steps, 0, 1)
+    times, sweeps = [], []
+    for i, p in enumerate(probs):
+        t, s = oracle_solve(p, args.tol)
+        log(f"oracle solve {i}: {t:.2f} s, {s} sweeps")
         if i >= args.warmup:
-            times.append(per)
-    sec = statistics.median(times) if times else float("nan")
-    v = 1.0 / sec if sec > 0 else 0.0
+            times.append(t)
+            sweeps.append(s)
+    total = sum(times)
+    v = len(times) / total if total > 0 else 0.0
+    desc = (f"each step one complete oracle solve (QTT assembly + AMEn to {args.tol:g}, NumPy/SciPy FP64) of an "
+            f"L={args.ref_L} plate of the same family; {len(times)} solves in {total:.1f} s")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"plate L={args.L} ({2 * 4 ** args.L} DOFs), clamped left, constant top-edge "
-                                   f"traction; (E, nu, amp, angle) from the held-out seed-2 set",
-                       "L": args.L, "batch": 1, "accept_rel_residual": args.tol},
+            "steps": len(times), "warmup": args.warmup, "ms_per_step": 1e3 * total / max(1, len(times)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args.ref_L), "L": args.ref_L, "batch": 1,
+                       "accept_rel_residual": args.tol,
+                       "note": "oracle solves at L=12 take minutes each; the level is the largest whose "
+                               "warm-up + timed solves fit a few minutes"},
             "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cpu_threads(), "kind": "oracle",
                              "sample": desc, "cpu": cpu_model()},
-            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "solve_stats": {"sweeps": sweeps, "seconds": [round(t, 3) for t in times]}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -310,8 +320,66 @@ def reference_main(args):
 # ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
-def main():
-    args = parse()
+def read_profile(lib):
+    import ctypes as C
+    out = {}
+    for cid, nm in CLASSES.items():
+        a, f_, b_, n_ = C.c_double(), C.c_double(), C.c_double(), C.c_longlong()
+        lib.qtt_profile_read(cid, C.byref(a), C.byref(f_), C.byref(b_), C.byref(n_))
+        out[nm] = [a.value, f_.value, b_.value, n_.value]
+    return out
+
+
+def measured_peaks(lib):
+    """FP64 and FP32 FMA rates of this GPU measured by the library's own
+    all-SM FMA-chain kernels (CUDA events), plus the measured HBM
+    copy and BF16 GEMM rates."""
+    import ctypes as C
+    import torch
+    peaks = {}
+    try:
+        peaks.update(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))))
+    except Exception:
+        pass
+    s = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for prec, key in ((0, "fp64_tflops"), (1, "fp32_tflops")):
+        v = C.c_double()
+        best = 0.0
+        for _ in range(3):
+            if lib.qtt_measure_fma_peak(prec, C.byref(v), s) == 0:
+                best = max(best, v.value)
+        peaks[key] = best
+    return peaks
+
+
+def roofline_of(prof, peaks, sms):
+    dom = max(prof, key=lambda k: prof[k][0])
+    ms, fl, by, n = prof[dom]
+    sec = ms / 1e3
+    if dom in ("gemm_f64", "qr_panel", "jacobi_svd", "lu_panel"):
+        bound, unit, peak = "alu", "TFLOP/s", peaks.get("fp64_tflops")
+        src = "FP64 FMA rate measured live by the library's all-SM FMA-chain kernel (qtt_measure_fma_peak)"
+        achieved = fl / 1e12 / sec if sec > 0 else 0.0
+    elif dom in ("gemm_f32", "pcg_f32"):
+        bound, unit, peak = "alu", "TFLOP/s", peaks.get("fp32_tflops")
+        src = "FP32 FMA rate measured live by the library's all-SM FMA-chain kernel (qtt_measure_fma_peak)"
+        achieved = fl / 1e12 / sec if sec > 0 else 0.0
+    else:
+        bound, unit, peak = "hbm", "GB/s", peaks.get("hbm_gbs", 6800.0)
+        src = "MEASURED_PEAKS.json hbm_gbs (driver-measured copy)"
+        achieved = by / 1e9 / sec if sec > 0 else 0.0
+    classes = {k: {"ms": round(v[0], 3), "gflop": round(v[1] / 1e9, 3), "gbytes": round(v[2] / 1e9, 3),
+                   "launches": int(v[3])} for k, v in prof.items()}
+    return {"bound": bound, "kernel": dom, "achieved": round(achieved, 4), "peak": round(peak, 3) if peak else None,
+            "unit": unit, "frac": round(achieved / peak, 5) if peak else None, "traffic": None,
+            "launches": int(n), "avg_launch_us": round(1e3 * ms / max(1, n), 2), "peak_source": src,
+            "sms": sms, "classes": classes,
+            "note": "per-class CUDA events bracket every launch of the timed steps on its own stream; "
+                    "achieved = algorithmic work of those launches / their summed event time"}
+
+
+def main(argv=None):
+    args = parse(argv)
     if args.impl == "reference":
         return reference_main(args)
     import ctypes as C
@@ -341,16 +409,19 @@ def main():
 
     global MAX_SWEEPS
     MAX_SWEEPS = args.max_sweeps
-    batch = args.batch or (2 if args.form == "fast" else 1)
+    batch = max(1, args.batch)
     nsteps = args.warmup + args.steps
     P, probs = workload(args.L, nsteps * batch, rank, world)
-    log(f"library ready; form {args.form}, L={args.L}, {batch} solves per step, {nsteps} steps")
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    log(f"library ready; form {args.form}, L={args.L}, {batch} solve(s) per step, {nsteps} steps, {sms} SMs")
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > 129 MB L2
+    peaks = measured_peaks(lib)
+    log(f"measured FMA peaks: FP64 {peaks.get('fp64_tflops', 0):.3f} TFLOP/s, "
+        f"FP32 {peaks.get('fp32_tflops', 0):.2f} TFLOP/s")
 
-    # one-time precompute (untimed): the warm-start network
     net, ws_info = None, None
-    if args.form == "fast" and args.warm_start and not args.no_warm_start:
+    if args.form == "fast" and args.warm_start:
         net, ws_info = train_warm_start(args.L, args.tol, args.train_steps)
         log(f"warm start ready: {ws_info}")
 
@@ -367,119 +438,115 @@ def main():
     launches0 = lib.qtt_kernel_launches()
     accepted = total = 0
     ms = 0.0
+    wall = 0.0
+    h2d = d2h = 0
     infos = []
+    prof = {k: [0.0, 0.0, 0.0, 0] for k in CLASSES.values()}
+    read_profile(lib)                      # drop anything recorded before
+    if not args.no_profile:
+        lib.qtt_profile_enable(1)
     barrier()
-    # lets ncu restrict a launch list to the timed region: the push/pop range
-    # covers this thread, the start/end range every thread (solve workers)
     torch.cuda.nvtx.range_push("timed")
     timed_range = torch.cuda.nvtx.range_start("timed")
     for st in range(args.warmup, nsteps):
         flush.zero_()
+        par, pr = step_slice(st)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         e0.record(stream)
-        us, inf = run_step(args.form, *step_slice(st), net, args.tol, args.workers)
+        us, inf = run_step(args.form, par, pr, net, args.tol, args.workers)
         e1.record(stream)
+        # end to end: the result (solution cores, host copies) read back
+        for u in us:
+            cores = u.cores()
+            d2h += sum(c.nbytes for c in cores)
         e1.synchronize()
-        ms += e0.elapsed_time(e1)
+        wall += time.perf_counter() - t0
+        h2d += sum(problem_bytes(p) for p in pr)
+        step_ms = e0.elapsed_time(e1)
+        ms += step_ms
+        if not args.no_profile:
+            for k, v in read_profile(lib).items():
+                prof[k] = [a + b for a, b in zip(prof[k], v)]
         for i in inf:
             total += 1
             accepted += int(0 < i["rel_residual"] <= args.tol)
             infos.append(i)
+        log(f"timed step {st - args.warmup}: {step_ms / 1e3:.2f} s, sweeps {[i['sweeps'] for i in inf]} "
+            f"res {[i['rel_residual'] for i in inf]}")
     torch.cuda.nvtx.range_end(timed_range)
     torch.cuda.nvtx.range_pop()
+    lib.qtt_profile_enable(0)
     barrier()
     launches = lib.qtt_kernel_launches() - launches0
     clocks = sampler.stop()
     ms_all, acc_all, tot_all, value = combine_ranks(ms, accepted, total, dist, device="cuda")
+    wall_all, acc_e2e, _, e2e_value = combine_ranks(1e3 * wall, accepted, total, dist, device="cuda")
+    log(f"timed: {ms_all:.1f} ms for {tot_all:.0f} solves ({acc_all:.0f} accepted); e2e wall {wall_all:.1f} ms")
+    roofline = roofline_of(prof, peaks, sms) if not args.no_profile else None
 
-    # ---- dominant kernel class: one extra step with CUDA events per launch
-    log(f"timed: {ms_all:.1f} ms for {tot_all:.0f} solves ({acc_all:.0f} accepted)")
-    lib.qtt_profile_enable(1)
-    run_step(args.form, *step_slice(nsteps - 1), net, args.tol, args.workers)
-    torch.cuda.synchronize()
-    lib.qtt_profile_enable(0)
-    classes = {0: "gemm_f64", 1: "gemm_f32", 2: "core_product", 3: "qr_panel", 4: "jacobi_svd", 5: "lu_panel",
-               6: "permute", 7: "to_full", 8: "pcg_f32"}
-    prof = {}
-    for cid, nm in classes.items():
-        a, f_, b_, n_ = C.c_double(), C.c_double(), C.c_double(), C.c_longlong()
-        lib.qtt_profile_read(cid, C.byref(a), C.byref(f_), C.byref(b_), C.byref(n_))
-        prof[nm] = {"ms": round(a.value, 3), "gflop": round(f_.value / 1e9, 3), "gbytes": round(b_.value / 1e9, 3),
-                    "launches": n_.value}
-    dom = max(prof, key=lambda k: prof[k]["ms"])
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    d = prof[dom]
-    sec = d["ms"] / 1e3
-    if dom in ("gemm_f64", "qr_panel", "jacobi_svd", "lu_panel"):
-        bound, peak, unit, src = "alu", 1.25, "TFLOP/s", "FP64 rate of GB300 (2 DFMA/SM/clk x 152 SMs x 2.07 GHz)"
-        achieved = d["gflop"] / 1e3 / sec if sec > 0 else 0.0
-    elif dom in ("gemm_f32", "pcg_f32"):
-        bound, peak, unit = "alu", 152 * 128 * 2 * 2.07e9 / 1e12, "TFLOP/s"
-        src = "FP32 SIMT: 152 SMs x 128 lanes x 2 flops x 2.07 GHz"
-        achieved = d["gflop"] / 1e3 / sec if sec > 0 else 0.0
-    else:
-        bound, peak, unit, src = "hbm", peaks.get("hbm_gbs", 6800.0), "GB/s", "MEASURED_PEAKS.json hbm_gbs"
-        achieved = d["gbytes"] / sec if sec > 0 else 0.0
-    roofline = {"bound": bound, "kernel": dom, "achieved": round(achieved, 4), "peak": round(peak, 2), "unit": unit,
-                "frac": round(achieved / peak, 5) if peak else None, "traffic": None,
-                "launches_in_profiled_step": d["launches"],
-                "avg_launch_us": round(1e3 * d["ms"] / max(1, d["launches"]), 2),
-                "peak_source": src, "classes": prof,
-                "note": "event-timed over one extra step of the same workload (events bracket every launch)"}
-
-    # ---- end to end through the public API, host buffers in and out
-    log(f"profiled step: dominant {dom}")
-    e2e = None
-    if not args.no_e2e:
-        h2d = d2h = 0
-        acc_e2e = 0
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for st in range(args.warmup, nsteps):
-            par, pr = step_slice(st)
-            h2d += par.nbytes + sum(8 * 2 + 4 * 4 + 24 for _ in pr)     # params / struct arrays per problem
-            us, inf = run_step(args.form, par, pr, net, args.tol, args.workers)
-            for u, i in zip(us, inf):
-                cores = u.cores()                                         # device -> host read of the result
-                d2h += sum(c.nbytes for c in cores)
-                acc_e2e += int(0 < i["rel_residual"] <= args.tol)
-        torch.cuda.synchronize()
-        te = time.perf_counter() - t0
-        e2e = {"value": acc_e2e / te if te > 0 else 0.0, "unit": "solves/s",
-               "h2d_bytes_per_step": h2d // max(1, args.steps), "d2h_bytes_per_step": d2h // max(1, args.steps)}
+    # ---- the plain FP64 form on the first problems of the timed set
+    plain = None
+    if args.form == "fast" and args.plain_solves > 0:
+        pms, pacc, pinfo = 0.0, 0, []
+        for j in range(args.plain_solves):
+            if time.perf_counter() - _T0 > args.plain_budget:
+                break
+            par, pr = step_slice(args.warmup + j % max(1, args.steps))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            _, inf = run_step("plain", par[:1], pr[:1], None, args.tol, 1)
+            e1.record(stream)
+            e1.synchronize()
+            pms += e0.elapsed_time(e1)
+            pacc += int(0 < inf[0]["rel_residual"] <= args.tol)
+            pinfo.append(inf[0])
+            log(f"plain solve {j}: {e0.elapsed_time(e1) / 1e3:.2f} s, sweeps {inf[0]['sweeps']}, "
+                f"refinements {inf[0]['refinements']}, res {inf[0]['rel_residual']:.3e}")
+        if pinfo:
+            pms_all, pacc_all, ptot_all, pvalue = combine_ranks(pms, pacc, len(pinfo), dist, device="cuda")
+            plain = {"value": pvalue, "unit": "solves/s", "solves": int(ptot_all), "accepted": int(pacc_all),
+                     "ms_per_solve": pms_all / max(1, len(pinfo)),
+                     "form": "FP64 AMEn (FP64 local CG), cold start, one solve at a time, FP64 outer refinement",
+                     "problems": "the first problem(s) of the timed set",
+                     "rel_residual": [i["rel_residual"] for i in pinfo], "sweeps": [i["sweeps"] for i in pinfo],
+                     "refinements": [i["refinements"] for i in pinfo],
+                     "fast_over_plain": (value / pvalue) if pvalue > 0 else None}
 
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return 0
 
-    log(f"e2e: {e2e}")
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        gs = int(statistics.median([i["sweeps"] for i in infos])) if infos else None
-        per, desc = oracle_sample(probs[args.warmup], args.tol, args.cpu_budget, sweeps_needed=gs)
-        cpu = {"value": 1.0 / per, "unit": "solves/s", "cores": cpu_threads(), "kind": "oracle", "sample": desc,
-               "cpu": cpu_model()}
+        cpu = cpu_baseline(args.ref_L, args.tol, args.cpu_solves)
+        log(f"cpu baseline: {cpu['value']:.4f} solves/s at L={args.ref_L}")
 
+    e2e = {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d // max(1, args.steps),
+           "d2h_bytes_per_step": d2h // max(1, args.steps),
+           "what": "host wall time of each timed step: host problem description -> assembly, solve and FP64 "
+                   "check through the C ABI -> solution cores copied to host memory"}
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_all / max(1, args.steps), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.form == "fast" else "f64",
             "data": "synthetic",
-            "config": {"workload": f"plate L={args.L} ({2 * 4 ** args.L} DOFs), clamped left, constant top-edge "
-                                   f"traction; (E, nu, amp, angle) from the held-out seed-2 set",
-                       "form": args.form, "L": args.L, "batch_per_rank": batch, "workers": args.workers,
+            "config": {"workload": workload_name(args.L), "form": args.form, "L": args.L,
+                       "batch_per_rank": batch, "workers": args.workers if batch > 1 else 1,
                        "learned_warm_start": ws_info is not None and bool(ws_info.get("used")),
                        "accept_rel_residual": args.tol, "l2": "flushed (256 MB write) before every timed step"},
             "accepted": int(acc_all), "solved": int(tot_all),
             "solve_stats": {"sweeps": [i["sweeps"] for i in infos], "max_rank": [i["max_rank"] for i in infos],
                             "rel_residual": [i["rel_residual"] for i in infos],
+                            "refinements": [i["refinements"] for i in infos],
                             "local_iters": [i["local_iters"] for i in infos]},
-            "warm_start": ws_info, "gpu_launches": int(launches), "clocks": clocks, "roofline": roofline,
+            "plain": plain, "warm_start": ws_info, "gpu_launches": int(launches), "clocks": clocks,
+            "roofline": roofline, "peaks": {k: peaks.get(k) for k in ("fp64_tflops", "fp32_tflops", "hbm_gbs",
+                                                                       "bf16_tflops")},
             "cpu_baseline": cpu, "e2e": e2e}
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -326,6 +326,17 @@ int qtt_ws_to_tensor(const float* out_row, int d, const int* modes, int r, doubl
 /* Number of CUDA kernels this library has launched in this process. */
 unsigned long long qtt_kernel_launches(void);
 
+/* Number of device allocations (stream-ordered or not) this library has
+ * made in this process. */
+unsigned long long qtt_device_allocations(void);
+
+/* Rate of this GPU's FMA pipe in precision prec (QTT_F64 or QTT_F32), in
+ * TFLOP/s (one FMA = 2 flops): eight independent FMA chains per thread in 8
+ * blocks of 256 threads per SM, timed with CUDA events on `stream` (the
+ * second of two launches).  The roofline denominator of the ALU-bound
+ * kernels; allocates and frees a small device buffer; synchronises. */
+int qtt_measure_fma_peak(int prec, double* tflops, void* stream);
+
 /* on != 0: bracket every launch of the profiled kernel classes with CUDA
  * events on its stream and record its algorithmic flops and bytes (adds
  * launch overhead; off by default).  Classes: 0 FP64 GEMM, 1 FP32 GEMM,

@@ -74,6 +74,8 @@ SIGNATURES = {
     "qtt_ws_adam": (C.c_int, [C.c_int, P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int, P]),
     "qtt_ws_to_tensor": (C.c_int, [P, C.c_int, IP, C.c_int, C.c_double, PP, P]),
     "qtt_kernel_launches": (C.c_ulonglong, []),
+    "qtt_device_allocations": (C.c_ulonglong, []),
+    "qtt_measure_fma_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double), P]),
     "qtt_profile_enable": (C.c_int, [C.c_int]),
     "qtt_profile_read": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
                                    C.POINTER(C.c_longlong)]),

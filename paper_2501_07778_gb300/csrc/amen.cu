@@ -38,7 +38,7 @@ namespace {
 using Tptr = std::unique_ptr<qtt_tensor, void (*)(qtt_tensor*)>;
 Tptr own(qtt_tensor* t) { return Tptr(t, tensor_free); }
 
-inline int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 4864)); }
+inline int grid_for(long long n) { return grid_for_n(n, 32); }
 
 // growable device buffer
 template <typename T>
@@ -75,6 +75,7 @@ struct DBuf {
     if (p) cudaFreeAsync(p, s);
     p = nullptr;
     size_t c = std::max<size_t>(n, cap * 3 / 2);
+    count_alloc();
     cudaError_t e = cudaMallocAsync(&p, c * sizeof(T), s);
     if (e != cudaSuccess) {
       cudaGetLastError();

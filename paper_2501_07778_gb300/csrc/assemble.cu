@@ -34,7 +34,7 @@ namespace {
 using Tptr = std::unique_ptr<qtt_tensor, void (*)(qtt_tensor*)>;
 Tptr own(qtt_tensor* t) { return Tptr(t, tensor_free); }
 
-inline int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 4864)); }
+inline int grid_for(long long n) { return grid_for_n(n, 32); }
 
 // ---------------------------------------------------------------------------
 // Closed-form 1D cores (LSB first).  Matrix cores are (r0, 2, 2, r1)

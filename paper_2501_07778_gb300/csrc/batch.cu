@@ -1,7 +1,7 @@
 // qtt_solve_batched: many independent solves (uneven levels, patch counts
 // and ranks) drained from one work queue by worker threads, each issuing its
 // solve's kernels on its own non-blocking stream.  One AMEn step is a chain
-// of small dependent contractions that cannot fill 152 SMs, so concurrent
+// of small dependent contractions that cannot fill the SMs, so concurrent
 // solves are what keeps the GPU busy; the caller's stream waits on every
 // worker stream before the call returns its results.
 #include <atomic>

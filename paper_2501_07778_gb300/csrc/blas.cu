@@ -197,10 +197,7 @@ __global__ void dot_kernel(const T* __restrict__ x, const T* __restrict__ y, siz
   }
 }
 
-inline int grid_for(long long n, int block = 256) {
-  long long g = (n + block - 1) / block;
-  return (int)std::max<long long>(1, std::min<long long>(g, 152LL * 16));
-}
+inline int grid_for(long long n, int block = 256) { return grid_for_n(n, 16, block); }
 }  // namespace
 
 template <typename T>
@@ -219,11 +216,12 @@ void gemm(cudaStream_t s, bool tA, bool tB, int M, int N, int K, T alpha, const 
     }
     return;
   }
-  // split K when the output tiles alone cannot fill the 152 SMs twice over
+  // split K when the output tiles alone cannot fill the SMs twice over
   const long long tiles = (long long)((M + GBM - 1) / GBM) * ((N + GBN - 1) / GBN) * batch;
+  const long long two_waves = 2LL * num_sms();
   int splits = 1;
-  if (tiles < 304 && K >= 256) {
-    long long want = (304 + tiles - 1) / tiles;
+  if (tiles < two_waves && K >= 256) {
+    long long want = (two_waves + tiles - 1) / tiles;
     splits = (int)std::min<long long>(want, (K + 127) / 128);
     splits = std::max(1, std::min(splits, 65535 / std::max(1, batch)));
   }
@@ -305,7 +303,7 @@ template <typename T>
 void sumsq(cudaStream_t s, const T* x, size_t n, double* out) {
   QTT_CUDA(cudaMemsetAsync(out, 0, sizeof(double), s));
   if (n == 0) return;
-  dot_kernel<T><<<std::min(grid_for((long long)n), 304), 256, 0, s>>>(x, (const T*)nullptr, n, out);
+  dot_kernel<T><<<std::min(grid_for((long long)n), 2 * num_sms()), 256, 0, s>>>(x, (const T*)nullptr, n, out);
   QTT_CHECK_LAUNCH();
 }
 
@@ -313,7 +311,7 @@ template <typename T>
 void dotp(cudaStream_t s, const T* x, const T* y, size_t n, double* out) {
   QTT_CUDA(cudaMemsetAsync(out, 0, sizeof(double), s));
   if (n == 0) return;
-  dot_kernel<T><<<std::min(grid_for((long long)n), 304), 256, 0, s>>>(x, y, n, out);
+  dot_kernel<T><<<std::min(grid_for((long long)n), 2 * num_sms()), 256, 0, s>>>(x, y, n, out);
   QTT_CHECK_LAUNCH();
 }
 
@@ -397,7 +395,7 @@ void einsum(cudaStream_t s, Arena& ar, const char* spec, const T* A, const int* 
   if (nFA == 0 || nFB == 0 || nBt == 0) return;
   {
     ContractArgs ca{};
-    if (plan_contract(spec, dA, dB, (int)sizeof(T), 304, ca)) {
+    if (plan_contract(spec, dA, dB, (int)sizeof(T), 2LL * num_sms(), ca)) {
       const long long items = contract_items(ca);
       ProfToken pt = prof_begin(sizeof(T) == 8 ? PROF_GEMM_F64 : PROF_GEMM_F32, s);
       if (ca.splits > 1) {

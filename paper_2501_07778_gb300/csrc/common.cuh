@@ -37,6 +37,8 @@ void set_last_error(const std::string& msg);
 // every kernel launch of the library is followed by this check, which also
 // counts the launch (qtt_kernel_launches)
 void count_launch();
+// every device allocation of the library is counted (qtt_device_allocations)
+void count_alloc();
 #define QTT_CHECK_LAUNCH()       \
   do {                           \
     ::qtt::count_launch();       \
@@ -53,6 +55,16 @@ struct ProfToken {
 bool prof_on();
 ProfToken prof_begin(int cls, cudaStream_t s);
 void prof_end(const ProfToken& t, cudaStream_t s, double flops, double bytes);
+
+// Streaming multiprocessors of the current device (queried once per device).
+int num_sms();
+// Grid for a grid-strided loop over n elements: one thread per element, at
+// most per_sm blocks per SM.
+inline int grid_for_n(long long n, int per_sm, int block = 256) {
+  const long long cap = (long long)num_sms() * per_sm;
+  long long g = (n + block - 1) / block;
+  return (int)(g < 1 ? 1 : (g < cap ? g : cap));
+}
 
 #define QTT_REQUIRE(cond, msg)                                             \
   do {                                                                     \
@@ -71,6 +83,7 @@ class Arena {
   void* raw(size_t bytes) {
     if (bytes == 0) bytes = 16;
     void* p = nullptr;
+    count_alloc();
     cudaError_t e = cudaMallocAsync(&p, bytes, stream_);
     if (e != cudaSuccess) {
       cudaGetLastError();

@@ -133,7 +133,7 @@ __global__ void upper_copy_kernel(const T* A, int lda, T* R, int ldr, int k, int
   }
 }
 
-inline int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 2432)); }
+inline int grid_for(long long n) { return grid_for_n(n, 16); }
 
 // ---------------------------------------------------------------------------
 // One-sided Jacobi on W (m x n, ldw) accumulating V (n x n, ldv); single CTA.

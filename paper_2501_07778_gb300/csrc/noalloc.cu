@@ -45,6 +45,9 @@ void* device_scratch() {
   if (g_scratch_ptr[dev] == nullptr) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_full_scratch);
+    // clear the runtime's sticky last-error slot so that the next library
+    // call does not report this failure as its own
+    if (e != cudaSuccess) cudaGetLastError();
     if (e != cudaSuccess || p == nullptr)
       throw qtt::QttError(QTT_ECUDA, std::string("qtt_to_full_noalloc: scratch lookup failed: ") +
                                          cudaGetErrorString(e));

@@ -48,7 +48,7 @@ __global__ void gaussian_kernel(double* out, long long n, unsigned long long see
 
 __global__ void set_scalar_kernel(double* p, double v) { *p = v; }
 
-inline int blocks_for(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 8)); }
+inline int blocks_for(long long n) { return grid_for_n(n, 8); }
 
 }  // namespace
 

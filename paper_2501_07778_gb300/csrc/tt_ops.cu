@@ -66,6 +66,7 @@ qtt_tensor* tensor_alloc(int d, const int* n, const int* m, const int* r, int pr
     for (int k = 0; k < d; ++k) {
       size_t e = core_elems(t, k);
       t->cap[k] = e;
+      count_alloc();
       cudaError_t err = cudaMallocAsync(&t->core[k], std::max<size_t>(e, 1) * esize(prec), t->stream);
       if (err != cudaSuccess) {
         cudaGetLastError();
@@ -93,6 +94,7 @@ void tensor_reserve(qtt_tensor* t, int k, size_t elems, cudaStream_t s) {
   // the old core is dead: released in order on s, replaced by a new block
   if (t->core[k]) QTT_CUDA(cudaFreeAsync(t->core[k], s));
   t->core[k] = nullptr;
+  count_alloc();
   QTT_CUDA(cudaMallocAsync(&t->core[k], elems * esize(t->prec), s));
   t->cap[k] = elems;
   t->stream = s;
@@ -118,7 +120,7 @@ qtt_tensor* tensor_clone(const qtt_tensor* src, int prec, cudaStream_t s) {
 // Kernels
 // ---------------------------------------------------------------------------
 namespace {
-inline int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 32)); }
+inline int grid_for(long long n) { return grid_for_n(n, 32); }
 
 // Y[(a + R0 g), i, k, (b + R1 e)] = sum_j A[a, i, j, b] X[g, j, k, e]
 // (X has an extra column mode p = 1 for an MPS operand).

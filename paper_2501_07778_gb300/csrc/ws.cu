@@ -18,7 +18,7 @@
 namespace qtt {
 namespace {
 
-inline int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 4864)); }
+inline int grid_for(long long n) { return grid_for_n(n, 32); }
 
 __global__ void bias_tanh_kernel(float* a, const float* b, int H, int B) {
   long long total = (long long)H * B;
@@ -273,7 +273,7 @@ int qtt_ws_adam(int n, float* w, const float* g, float* m, float* v, float lr, f
   QTT_REQUIRE(n > 0 && w && g && m && v && t >= 1, "qtt_ws_adam: bad argument");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
-  adam_kernel<<<std::min((n + 255) / 256, 4864), 256, 0, s>>>(n, w, g, m, v, lr, b1, b2, eps, c1, c2);
+  adam_kernel<<<grid_for(n), 256, 0, s>>>(n, w, g, m, v, lr, b1, b2, eps, c1, c2);
   QTT_CHECK_LAUNCH();
   return QTT_OK;
   WS_END

@@ -68,3 +68,49 @@ def test_mlp_backward_finite_difference():
 def test_output_count_matches_plate_layout():
     """Rank-16 cores for the L = 12 plate: 4 x 16 + 11 x 16 x 4 x 16 + 16 x 2."""
     assert ws.n_outputs([4] * 12 + [2], 16) == 64 + 11 * 1024 + 32 == 11360
+
+
+def _adam_run(grads, lr=0.01, p0=0.0):
+    p = {"w": np.array([p0])}
+    state = {}
+    out = []
+    for t, g in enumerate(grads, start=1):
+        ws.adam_step(p, {"w": np.array([g])}, state, lr=lr, t=t)
+        out.append(float(p["w"][0]))
+    return out
+
+
+def test_adam_first_step_and_constant_gradient_move_by_lr():
+    """Kingma & Ba (2015), Sec. 2.1 and Alg. 1: with bias correction the first
+    update is lr * g / (|g| + eps), whatever |g|; under a constant gradient
+    m_hat = g and v_hat = g^2 at every step, so every step moves by the same
+    amount.  A wrong bias-correction power or swapped beta1/beta2 breaks
+    both."""
+    eps = 1e-8
+    for g in (3.7, -0.02, 250.0):
+        traj = _adam_run([g] * 5, lr=0.01)
+        step = 0.01 * abs(g) / (abs(g) + eps)
+        moves = np.diff([0.0] + traj)
+        np.testing.assert_allclose(moves, -np.sign(g) * step, rtol=1e-12)
+
+
+def test_adam_two_steps_by_hand():
+    """Gradients +1 then -1 with beta1 = 0.9, beta2 = 0.999 (Alg. 1 defaults),
+    worked by hand: m_1 = 0.1, v_1 = 0.001, m_hat_1 = 1, v_hat_1 = 1;
+    m_2 = 0.09 - 0.1 = -0.01, m_hat_2 = -0.01 / 0.19 = -1/19;
+    v_2 = 0.000999 + 0.001 = 0.001999, v_hat_2 = 0.001999 / (1 - 0.998001) = 1.
+    So p_1 = -lr / (1 + eps) and p_2 = p_1 + lr / (19 (1 + eps))."""
+    lr, eps = 0.01, 1e-8
+    p1, p2 = _adam_run([1.0, -1.0], lr=lr)
+    assert abs(p1 - (-lr / (1 + eps))) <= 1e-15
+    assert abs(p2 - (p1 + lr / (19.0 * (1 + eps)))) <= 1e-15
+
+
+def test_adam_invariant_to_gradient_scale():
+    """The update is invariant to a positive rescaling of the gradients
+    (Kingma & Ba, Sec. 2.1), up to the eps term."""
+    rng = np.random.default_rng(3)
+    gs = rng.standard_normal(6)
+    a = _adam_run(list(gs), lr=0.05)
+    b = _adam_run(list(1e3 * gs), lr=0.05)
+    np.testing.assert_allclose(a, b, rtol=1e-6, atol=1e-9)

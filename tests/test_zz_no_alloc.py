@@ -1,13 +1,15 @@
 """The allocation-free Z-block expansion (qtt_to_full_noalloc, through the C
-ABI) against the ordinary one (qtt_to_full) on the same tensors, two calls in
-a row, plus its argument and size checks.  Collected last on purpose: the
-first call on a device sets up the fixed scratch buffer."""
+ABI) against the oracle's entry-wise expansion and against the ordinary
+qtt_to_full on the same tensors, two calls in a row; that the calls take no
+device memory; and its argument and size checks.  Collected last on purpose:
+the first call on a device sets up the fixed scratch buffer."""
 import ctypes as C
 
 import numpy as np
 import pytest
 
 import workloads as W
+from oracle import tt
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -27,18 +29,28 @@ CASES = [
 
 
 @pytest.mark.parametrize("modes,ranks,prec", CASES)
-def test_noalloc_matches_to_full_twice(modes, ranks, prec):
+def test_noalloc_matches_oracle_and_to_full_twice(modes, ranks, prec):
     cores = W.random_tt(11, modes, ranks)
     x = q.QTT.from_cores(cores, prec)
+    # the oracle expands the cores the library actually holds (FP32 cases
+    # are rounded on upload)
+    want = tt.full([np.asarray(c, dtype=np.float64) for c in x.cores()])
     ref = q.qtt_to_full(x)
     tol = 1e-13 if prec == q.QTT_F64 else 1e-5
-    scale = float(ref.abs().max())
+    scale = float(np.abs(want).max())
+    lib = _lib.load()
+    out = torch.full_like(ref, float("nan"))
+    q.qtt_to_full_noalloc(x, out)          # the first call may set up the buffer
+    torch.cuda.synchronize()
     for _ in range(2):
         out = torch.full_like(ref, float("nan"))
+        allocs = lib.qtt_device_allocations()
         q.qtt_to_full_noalloc(x, out)
         torch.cuda.synchronize()
-        err = float((out - ref).abs().max())
-        assert err <= tol * scale, err
+        assert lib.qtt_device_allocations() == allocs, "qtt_to_full_noalloc took device memory"
+        got = out.double().cpu().numpy()
+        assert float(np.abs(got - want).max()) <= tol * scale
+        assert float((out - ref).abs().max()) <= tol * scale
 
 
 def test_noalloc_rejects_oversized_and_mpo():
@@ -62,7 +74,8 @@ def test_noalloc_rejects_oversized_and_mpo():
     rc = lib.qtt_to_full_noalloc(A.handle, C.c_void_p(buf.data_ptr()), 8, s)
     assert rc == _lib.QTT_EINVAL
     # the library still works afterwards
-    y = q.QTT.from_cores(W.random_tt(4, [4, 4, 2], [1, 3, 2, 1]))
+    cores = W.random_tt(4, [4, 4, 2], [1, 3, 2, 1])
+    y = q.QTT.from_cores(cores)
     o = torch.empty(32, dtype=torch.float64, device="cuda")
     q.qtt_to_full_noalloc(y, o)
-    torch.testing.assert_close(o, q.qtt_to_full(y), rtol=1e-13, atol=1e-14)
+    np.testing.assert_allclose(o.cpu().numpy(), tt.full(cores), rtol=1e-13, atol=1e-14)
