@@ -52,7 +52,7 @@ ACCEPT = 1e-8
 MAX_SWEEPS = 24
 _T0 = time.perf_counter()
 CLASSES = {0: "gemm_f64", 1: "gemm_f32", 2: "core_product", 3: "qr_panel", 4: "jacobi_svd", 5: "lu_panel",
-           6: "permute", 7: "to_full", 8: "pcg_f32"}
+           6: "permute", 7: "to_full", 8: "pcg_f32", 9: "jacobi_f32"}
 
 
 def log(msg: str):
@@ -360,7 +360,7 @@ def roofline_of(prof, peaks, sms):
         bound, unit, peak = "alu", "TFLOP/s", peaks.get("fp64_tflops")
         src = "FP64 FMA rate measured live by the library's all-SM FMA-chain kernel (qtt_measure_fma_peak)"
         achieved = fl / 1e12 / sec if sec > 0 else 0.0
-    elif dom in ("gemm_f32", "pcg_f32"):
+    elif dom in ("gemm_f32", "pcg_f32", "jacobi_f32"):
         bound, unit, peak = "alu", "TFLOP/s", peaks.get("fp32_tflops")
         src = "FP32 FMA rate measured live by the library's all-SM FMA-chain kernel (qtt_measure_fma_peak)"
         achieved = fl / 1e12 / sec if sec > 0 else 0.0
@@ -475,7 +475,8 @@ def main(argv=None):
             accepted += int(0 < i["rel_residual"] <= args.tol)
             infos.append(i)
         log(f"timed step {st - args.warmup}: {step_ms / 1e3:.2f} s, sweeps {[i['sweeps'] for i in inf]} "
-            f"res {[i['rel_residual'] for i in inf]}")
+            f"res {[i['rel_residual'] for i in inf]} checks {[i['checks'] for i in inf]} "
+            f"check_ms {[round(i['check_ms']) for i in inf]} refine_ms {[round(i['refine_ms']) for i in inf]}")
     torch.cuda.nvtx.range_end(timed_range)
     torch.cuda.nvtx.range_pop()
     lib.qtt_profile_enable(0)
@@ -543,7 +544,10 @@ def main(argv=None):
             "solve_stats": {"sweeps": [i["sweeps"] for i in infos], "max_rank": [i["max_rank"] for i in infos],
                             "rel_residual": [i["rel_residual"] for i in infos],
                             "refinements": [i["refinements"] for i in infos],
-                            "local_iters": [i["local_iters"] for i in infos]},
+                            "local_iters": [i["local_iters"] for i in infos],
+                            "checks": [i["checks"] for i in infos],
+                            "check_ms": [round(i["check_ms"], 1) for i in infos],
+                            "refine_ms": [round(i["refine_ms"], 1) for i in infos]},
             "plain": plain, "warm_start": ws_info, "gpu_launches": int(launches), "clocks": clocks,
             "roofline": roofline, "peaks": {k: peaks.get(k) for k in ("fp64_tflops", "fp32_tflops", "hbm_gbs",
                                                                        "bf16_tflops")},

@@ -232,6 +232,10 @@ typedef struct {
   double max_local_res;   /* last sweep's maximum local relative residual */
   double rel_residual;    /* FP64 ||f - K u|| / ||f|| (computed when tol > 0) */
   double erank;           /* effective rank of the solution (Section 4) */
+  int checks;             /* FP64 global residual evaluations */
+  double check_ms;        /* host wall time of those evaluations */
+  double refine_ms;       /* host wall time of the outer refinement steps
+                             (residual rounding, correction solve, update) */
 } qtt_solve_info;
 
 /* Solve K u = f.  x0: initial guess (NULL = rank-1 constant); z0: initial
@@ -342,7 +346,8 @@ int qtt_measure_fma_peak(int prec, double* tflops, void* stream);
  * launch overhead; off by default).  Classes: 0 FP64 GEMM, 1 FP32 GEMM,
  * 2 MPO x MPS core product, 3 Householder panel, 4 Jacobi SVD, 5 LU panel,
  * 6 permutation, 7 full expansion, 8 persistent FP32 local CG (one launch runs
- * all iterations of a CG cycle). */
+ * all iterations of a CG cycle), 9 FP32 Jacobi sweeps of the mixed-precision
+ * SVD (class 4 then holds the FP64 sweeps). */
 int qtt_profile_enable(int on);
 
 /* Sum of event-timed milliseconds, algorithmic flops and bytes, and launch

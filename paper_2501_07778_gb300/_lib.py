@@ -39,7 +39,8 @@ class QttSolveOpts(C.Structure):
 class QttSolveInfo(C.Structure):
     _fields_ = [("status", C.c_int), ("sweeps", C.c_int), ("local_solves", C.c_int), ("local_iters", C.c_int),
                 ("max_rank", C.c_int), ("refinements", C.c_int), ("max_local_res", C.c_double),
-                ("rel_residual", C.c_double), ("erank", C.c_double)]
+                ("rel_residual", C.c_double), ("erank", C.c_double), ("checks", C.c_int),
+                ("check_ms", C.c_double), ("refine_ms", C.c_double)]
 
 
 P = C.c_void_p

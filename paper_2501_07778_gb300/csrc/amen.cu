@@ -35,6 +35,18 @@ namespace qtt {
 double residual64(cudaStream_t s, const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* f);
 namespace {
 
+// residual64 with its count and host wall time recorded in the solve record
+double timed_residual64(cudaStream_t s, const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* f,
+                        qtt_solve_info* info) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const double rel = residual64(s, K, u, f);
+  if (info) {
+    info->checks += 1;
+    info->check_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return rel;
+}
+
 using Tptr = std::unique_ptr<qtt_tensor, void (*)(qtt_tensor*)>;
 Tptr own(qtt_tensor* t) { return Tptr(t, tensor_free); }
 
@@ -875,7 +887,7 @@ struct Amen {
       // It is measured again only after the local residuals have halved.
       if (sizeof(T) == 8 && global_check > 0 && max_res <= global_check * tol && max_res <= 0.5 * checked_at) {
         checked_at = max_res;
-        const double rel = residual64(s, A, x, y);
+        const double rel = timed_residual64(s, A, x, y, info);
         if (info) info->rel_residual = rel;
         if (verbose)
           fprintf(stderr, "[qtt_solve f64 %.2fs] sweep %d global FP64 rel residual %.3e\n",
@@ -1054,13 +1066,14 @@ int solve(const qtt_tensor* K, const qtt_tensor* f, const qtt_tensor* x0, const 
       // <= tol is the final iterate's residual; otherwise measure it now
       const double rel = (it == 0 && rc == QTT_OK && inf->rel_residual > 0 && inf->rel_residual <= o.tol)
                              ? inf->rel_residual
-                             : residual64(s, K, u.get(), f);
+                             : timed_residual64(s, K, u.get(), f, inf);
       inf->rel_residual = rel;
       if (o.verbose) fprintf(stderr, "[qtt_solve] check %d: FP64 rel residual %.3e\n", it, rel);
       if (rel <= o.tol || it >= refine_max) {
         rc = rel <= o.tol ? QTT_OK : QTT_ENOCONV;
         break;
       }
+      const auto t_ref = std::chrono::steady_clock::now();
       if (fnorm < 0) {
         Arena ar(s);
         fnorm = norm<double>(s, ar, f);
@@ -1090,7 +1103,9 @@ int solve(const qtt_tensor* K, const qtt_tensor* f, const qtt_tensor* x0, const 
       u = own(tt_sum<double>(s, 1.0, u.get(), 1.0, d.get()));
       Arena ar(s);
       round_tt<double>(s, ar, u.get(), 1e-14, o.max_rank > 0 ? o.max_rank : 0);
+      QTT_CUDA(cudaStreamSynchronize(s));
       inf->refinements += 1;
+      inf->refine_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_ref).count();
     }
     *xout = u.release();
   }

@@ -9,6 +9,8 @@
 #include <algorithm>
 #include <cmath>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 
 namespace qtt {
@@ -201,6 +203,81 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int m, int n, T* W, int ld
   if (threadIdx.x == 0 && sweeps_out) *sweeps_out = sweep;
 }
 
+// ---------------------------------------------------------------------------
+// The same one-sided Jacobi sweeps on many SMs: the np/2 pairs of a round go
+// to the warps of the whole grid (one pair per warp, one warp per CTA while
+// the pairs fit the SMs), so the FP64 dot products and rotations of a round
+// run on up to np/2 SMs instead of one; a grid barrier separates the rounds.
+// Column data written in one round is read by other SMs in the next, so the
+// loads bypass L1 (__ldcg).  rot[s] counts the warps that rotated in sweep s
+// (zeroed by the host); every thread reads it after the sweep's last
+// barrier, so all CTAs take the same stop decision.  Cooperative launch only.
+// ---------------------------------------------------------------------------
+template <typename T, typename Acc>
+__global__ void jacobi_coop_kernel(int m, int n, T* W, int ldw, T* Vm, int ldv, int max_sweeps, unsigned* rot,
+                                   int* sweeps_out) {
+  cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  const int gw = blockIdx.x * wpb + (threadIdx.x >> 5);
+  const int nwarps = gridDim.x * wpb;
+  const int np = n + (n & 1);
+  const Acc tol = (Acc)(1e-15 * (double)(m > 1 ? m : 1));
+  const Acc tolf = (sizeof(T) == 4) ? (Acc)(1e-7 * (double)(m > 1 ? m : 1)) : tol;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    bool any = false;
+    for (int round = 0; round < np - 1; ++round) {
+      for (int pi = gw; pi < np / 2; pi += nwarps) {
+        int p, q;
+        if (pi == 0) {
+          p = round % (np - 1);
+          q = np - 1;
+        } else {
+          p = (round + pi) % (np - 1);
+          q = (round - pi + (np - 1)) % (np - 1);
+        }
+        if (p > q) { int t = p; p = q; q = t; }
+        if (q >= n) continue;
+        T* wp = W + (long long)p * ldw;
+        T* wq = W + (long long)q * ldw;
+        Acc al = 0, be = 0, ga = 0;
+        for (int i = lane; i < m; i += 32) {
+          Acc a = __ldcg(wp + i), b = __ldcg(wq + i);
+          al += a * a;
+          be += b * b;
+          ga += a * b;
+        }
+        al = wsum(al);
+        be = wsum(be);
+        ga = wsum(ga);
+        if (ga == (Acc)0 || !(fabs(ga) > tolf * sqrt(al * be))) continue;
+        Acc zeta = (be - al) / ((Acc)2 * ga);
+        Acc t = (zeta >= (Acc)0 ? (Acc)1 : (Acc)-1) / (fabs(zeta) + sqrt((Acc)1 + zeta * zeta));
+        Acc cs = (Acc)1 / sqrt((Acc)1 + t * t), sn = cs * t;
+        for (int i = lane; i < m; i += 32) {
+          Acc a = __ldcg(wp + i), b = __ldcg(wq + i);
+          wp[i] = (T)(cs * a - sn * b);
+          wq[i] = (T)(sn * a + cs * b);
+        }
+        T* vp = Vm + (long long)p * ldv;
+        T* vq = Vm + (long long)q * ldv;
+        for (int i = lane; i < n; i += 32) {
+          Acc a = __ldcg(vp + i), b = __ldcg(vq + i);
+          vp[i] = (T)(cs * a - sn * b);
+          vq[i] = (T)(sn * a + cs * b);
+        }
+        any = true;
+      }
+      grid.sync();
+    }
+    if (any && lane == 0) atomicAdd(&rot[sweep], 1u);
+    grid.sync();
+    if (*(volatile unsigned*)&rot[sweep] == 0u) break;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && sweeps_out) *sweeps_out = sweep;
+}
+
 // column norms -> S, normalise W columns, then sort descending (order[])
 template <typename T>
 __global__ void __launch_bounds__(1024) svd_finish_kernel(int m, int n, T* W, int ldw, T* S, int* order) {
@@ -343,6 +420,38 @@ __global__ void trsv_block_kernel(int nb, const T* A, int lda, T* X, int ldx, in
 
 }  // namespace
 
+// FP64 (or FP32) one-sided Jacobi sweeps on W (m x n) accumulating V: the
+// cooperative many-SM kernel when the device supports cooperative launch
+// and there are enough pairs to spread, else the single-CTA kernel.
+template <typename T, typename Acc>
+void jacobi_sweeps(cudaStream_t s, Arena& ar, int m, int n, T* W, int ldw, T* Vm, int ldv, int max_sweeps) {
+  static int coop = -1;
+  if (coop < 0) {
+    int dev = 0, v = 0;
+    coop = (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && v) ? 1 : 0;
+    cudaGetLastError();
+  }
+  const int pairs = (n + (n & 1)) / 2;
+  if (!coop || pairs < 8) {
+    jacobi_kernel<T, Acc><<<1, 1024, 0, s>>>(m, n, W, ldw, Vm, ldv, max_sweeps, nullptr);
+    QTT_CHECK_LAUNCH();
+    return;
+  }
+  // one warp per pair; one warp per CTA while the pairs fit the SMs
+  const int sms = num_sms();
+  const int wpb = std::min(8, (pairs + sms - 1) / sms);
+  int occ = 0;
+  QTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_coop_kernel<T, Acc>, 32 * wpb, 0));
+  const int grid = std::max(1, std::min((pairs + wpb - 1) / wpb, sms * std::max(1, occ)));
+  unsigned* rot = ar.alloc<unsigned>(max_sweeps);
+  QTT_CUDA(cudaMemsetAsync(rot, 0, sizeof(unsigned) * max_sweeps, s));
+  int* none = nullptr;
+  void* args[] = {&m, &n, &W, &ldw, &Vm, &ldv, &max_sweeps, &rot, &none};
+  QTT_CUDA(cudaLaunchCooperativeKernel((void*)jacobi_coop_kernel<T, Acc>, grid, 32 * wpb, args, 0, s));
+  count_launch();
+}
+
 template <typename T>
 void qr(cudaStream_t s, Arena& ar, int m, int n, T* A, int lda, T* Q, int ldq, T* R, int ldr) {
   QTT_REQUIRE(m >= 1 && n >= 1, "qr: empty matrix");
@@ -438,7 +547,7 @@ void svd(cudaStream_t s, Arena& ar, int m, int n, T* A, int lda, T* U, int ldu, 
     convert<T, float>(s, R, R32, (size_t)k * n);
     set_identity_kernel<float><<<grid_for((long long)n * n), 256, 0, s>>>(V32, n, n, n);
     QTT_CHECK_LAUNCH();
-    ProfToken pf = prof_begin(PROF_JACOBI, s);
+    ProfToken pf = prof_begin(PROF_JACOBI_F32, s);
     jacobi_kernel<float, float><<<1, 1024, 0, s>>>(k, n, R32, k, V32, n, 40, nullptr);
     QTT_CHECK_LAUNCH();
     if (pf.ev) prof_end(pf, s, 0.5 * n * (n - 1) * (6.0 * k + 12.0 * k + 12.0 * n), 4.0 * 2.0 * (k + n) * n);
@@ -461,14 +570,12 @@ void svd(cudaStream_t s, Arena& ar, int m, int n, T* A, int lda, T* U, int ldu, 
     set_identity_kernel<T><<<grid_for((long long)n * n), 256, 0, s>>>(V2, n, n, n);
     QTT_CHECK_LAUNCH();
     ProfToken pj = prof_begin(PROF_JACOBI, s);
-    jacobi_kernel<T><<<1, 1024, 0, s>>>(k, n, R, k, V2, n, 40, nullptr);
-    QTT_CHECK_LAUNCH();
+    jacobi_sweeps<T, double>(s, ar, k, n, R, k, V2, n, 40);
     if (pj.ev) prof_end(pj, s, 0.5 * n * (n - 1) * (6.0 * k + 12.0 * k + 12.0 * n), sizeof(T) * 2.0 * (k + n) * n);
     gemm<T>(s, false, false, n, n, n, T(1), V0, n, 0, V2, n, 0, T(0), Vm, n, 0);
   } else {
-    ProfToken pj = prof_begin(PROF_JACOBI, s);
-    jacobi_kernel<T><<<1, 1024, 0, s>>>(k, n, R, k, Vm, n, 40, nullptr);
-    QTT_CHECK_LAUNCH();
+    ProfToken pj = prof_begin(sizeof(T) == 8 ? PROF_JACOBI : PROF_JACOBI_F32, s);
+    jacobi_sweeps<T, double>(s, ar, k, n, R, k, Vm, n, 40);
     // nominal work of one sweep over all pairs (the sweep count is data dependent)
     if (pj.ev) prof_end(pj, s, 0.5 * n * (n - 1) * (6.0 * k + 12.0 * k + 12.0 * n), sizeof(T) * 2.0 * (k + n) * n);
   }
