@@ -50,6 +50,7 @@ sys.path.insert(0, ROOT)
 METRIC = "QTT solves/sec at rel. residual 1e-8 (L=12); fast form vs plain FP64 GPU"
 ACCEPT = 1e-8
 MAX_SWEEPS = 24
+KICK_RANK = 8
 _T0 = time.perf_counter()
 CLASSES = {0: "gemm_f64", 1: "gemm_f32", 2: "core_product", 3: "qr_panel", 4: "jacobi_svd", 5: "lu_panel",
            6: "permute", 7: "to_full", 8: "pcg_f32", 9: "jacobi_f32"}
@@ -72,6 +73,7 @@ def parse(argv=None):
     ap.add_argument("--batch", type=int, default=1, help="problems per step per rank")
     ap.add_argument("--workers", type=int, default=1, help="concurrent solves when --batch > 1")
     ap.add_argument("--max-sweeps", type=int, default=24)
+    ap.add_argument("--kick-rank", type=int, default=8, help="residual-proxy rank of the AMEn enrichment")
     ap.add_argument("--L", type=int, default=12)
     ap.add_argument("--tol", type=float, default=ACCEPT)
     ap.add_argument("--plain-solves", type=int, default=1,
@@ -178,7 +180,7 @@ def combine_ranks(ms: float, accepted: int, total: int, dist=None, device: str =
 def solve_kw(form: str, tol: float):
     import paper_2501_07778_gb300 as q
     prec = q.QTT_F64 if form == "plain" else q.QTT_MIXED
-    return dict(tol=tol, precision=prec, kick_rank=8, max_sweeps=MAX_SWEEPS)
+    return dict(tol=tol, precision=prec, kick_rank=KICK_RANK, max_sweeps=MAX_SWEEPS)
 
 
 def problem_bytes(prob) -> int:
@@ -213,7 +215,8 @@ def train_warm_start(L: int, tol: float, steps: int):
     from paper_2501_07778_gb300 import warmstart as ws
     t0 = time.perf_counter()
     log(f"warm start: {2 * len(NU_GRID)} basis solves at L={L}")
-    basis64 = ws.basis_solutions(L, NU_GRID, tol=tol, precision=QTT_MIXED, kick_rank=8, max_sweeps=MAX_SWEEPS)
+    basis64 = ws.basis_solutions(L, NU_GRID, tol=tol, precision=QTT_MIXED, kick_rank=KICK_RANK,
+                                 max_sweeps=MAX_SWEEPS)
     basis = [b.copy(prec=QTT_F32) for b in basis64]
     t1 = time.perf_counter()
     log(f"warm start: basis solves took {t1 - t0:.1f} s; training {steps} steps")
@@ -407,8 +410,9 @@ def main(argv=None):
             dist.barrier()
         torch.cuda.synchronize()
 
-    global MAX_SWEEPS
+    global MAX_SWEEPS, KICK_RANK
     MAX_SWEEPS = args.max_sweeps
+    KICK_RANK = args.kick_rank
     batch = max(1, args.batch)
     nsteps = args.warmup + args.steps
     P, probs = workload(args.L, nsteps * batch, rank, world)
@@ -539,7 +543,8 @@ def main(argv=None):
             "config": {"workload": workload_name(args.L), "form": args.form, "L": args.L,
                        "batch_per_rank": batch, "workers": args.workers if batch > 1 else 1,
                        "learned_warm_start": ws_info is not None and bool(ws_info.get("used")),
-                       "accept_rel_residual": args.tol, "l2": "flushed (256 MB write) before every timed step"},
+                       "accept_rel_residual": args.tol, "kick_rank": args.kick_rank, "max_sweeps": args.max_sweeps,
+                       "l2": "flushed (256 MB write) before every timed step"},
             "accepted": int(acc_all), "solved": int(tot_all),
             "solve_stats": {"sweeps": [i["sweeps"] for i in infos], "max_rank": [i["max_rank"] for i in infos],
                             "rel_residual": [i["rel_residual"] for i in infos],

@@ -273,11 +273,25 @@ int qtt_solve_batched(int count, const qtt_tensor* const* K, const qtt_tensor* c
                       const qtt_tensor* const* x0, const qtt_solve_opts* opts, int nworkers,
                       qtt_tensor** x, qtt_solve_info* info, void* stream);
 
-/* FP64 relative residual ||f - K u|| / ||f||: the product K u and the sum are
- * formed in QTT and normed by orthogonalisation (no rounding).  Writes *out
- * on the host; synchronises the stream. */
+/* FP64 relative residual ||f - K u|| / ||f||: the product K u is formed
+ * exactly in QTT (ranks R r), the sum f - K u expanded to full format (or
+ * normed by orthogonalisation when above 2^28 entries), no rounding.  Writes
+ * *out on the host; synchronises the stream. */
 int qtt_residual(const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* f,
                  double* out, void* stream);
+
+/* The same relative residual with K applied as the finite-element operator
+ * it was assembled from (Sections 3.4-3.8): u and f are expanded to full
+ * format and K u is the Q1 plane-stress stencil of every patch, the
+ * concatenation rows of nodes held by several patch copies (summed stiffness
+ * rows plus gamma (cnt u_a - sum of the copies' u)) and the Dirichlet masks.
+ * Equal to qtt_residual up to the assembly's rounding of K, in O(N r)
+ * instead of O(N R r) flops.  K must come from qtt_assemble_stiffness and not
+ * have been rounded in place since (else QTT_EINVAL); u, f FP64 MPS.  This is
+ * the global residual qtt_solve checks for such K.  Writes *out on the host;
+ * synchronises the stream. */
+int qtt_residual_fe(const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* f,
+                    double* out, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Learned warm start (growth pattern of this engine; not in the paper)      */

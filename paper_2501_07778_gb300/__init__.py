@@ -19,7 +19,7 @@ from ._lib import (QTT_F32, QTT_F64, QTT_MIXED, QTT_ORDER_CANONICAL, QTT_ORDER_Z
                    QttSolveOpts)
 
 __all__ = ["QTT", "QttError", "qtt_assemble_stiffness", "qtt_matvec", "qtt_round", "qtt_solve", "qtt_to_full",
-           "qtt_axpby", "qtt_norm", "qtt_residual", "qtt_round_residual", "qtt_to_full_noalloc", "QTT_F64", "QTT_F32", "QTT_MIXED", "QTT_ORDER_Z_BLOCK",
+           "qtt_axpby", "qtt_norm", "qtt_residual", "qtt_residual_fe", "qtt_round_residual", "qtt_to_full_noalloc", "QTT_F64", "QTT_F32", "QTT_MIXED", "QTT_ORDER_Z_BLOCK",
            "QTT_ORDER_CANONICAL", "lib"]
 
 
@@ -188,6 +188,13 @@ def qtt_norm(x: QTT, stream=None) -> float:
 def qtt_residual(K: QTT, u: QTT, f: QTT, stream=None) -> float:
     v = C.c_double()
     _check(lib().qtt_residual(K.handle, u.handle, f.handle, C.byref(v), _stream(stream)), "qtt_residual")
+    return v.value
+
+
+def qtt_residual_fe(K: QTT, u: QTT, f: QTT, stream=None) -> float:
+    """||f - K u|| / ||f|| with K applied as its finite-element stencil."""
+    v = C.c_double()
+    _check(lib().qtt_residual_fe(K.handle, u.handle, f.handle, C.byref(v), _stream(stream)), "qtt_residual_fe")
     return v.value
 
 

@@ -33,13 +33,34 @@
 
 namespace qtt {
 double residual64(cudaStream_t s, const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* f);
+bool has_fe_operator(const qtt_tensor* K);
+double residual_fe(cudaStream_t s, const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* u2,
+                   const qtt_tensor* f);
 namespace {
 
-// residual64 with its count and host wall time recorded in the solve record
+// The FP64 global relative residual ||f - K (u + u2)|| / ||f|| (u2 may be
+// NULL): for an MPO from qtt_assemble_stiffness, K is applied in full format
+// as the finite-element operator it represents (fe_residual.cu, HBM-bound);
+// otherwise by the exact QTT product, expanded (residual64).  Its count and
+// host wall time go to the solve record.
 double timed_residual64(cudaStream_t s, const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* f,
-                        qtt_solve_info* info) {
+                        qtt_solve_info* info, const qtt_tensor* u2 = nullptr) {
   const auto t0 = std::chrono::steady_clock::now();
-  const double rel = residual64(s, K, u, f);
+  double rel;
+  if (has_fe_operator(K)) {
+    rel = residual_fe(s, K, u, u2, f);
+  } else if (u2) {
+    auto sum = tt_sum<double>(s, 1.0, u, 1.0, u2);
+    try {
+      rel = residual64(s, K, sum, f);
+    } catch (...) {
+      tensor_free(sum);
+      throw;
+    }
+    tensor_free(sum);
+  } else {
+    rel = residual64(s, K, u, f);
+  }
   if (info) {
     info->checks += 1;
     info->check_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -109,6 +130,27 @@ __global__ void scale_by_device_kernel(T* v, const T* src, int n, const double* 
   if (blockIdx.x == 0 && threadIdx.x == 0 && hout) *hout = h;
   double inv = h > 0 ? 1.0 / h : 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = (T)((double)src[i] * inv);
+}
+
+// out += sum_i (a_i - b_i)^2 with a in FP32 and b in T, accumulated in FP64
+template <typename T>
+__global__ void diff_sumsq_kernel(const float* __restrict__ a, const T* __restrict__ b, int n, double* out) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double d = (double)a[i] - (double)b[i];
+    acc += d * d;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) atomicAdd(out, v);
+  }
 }
 
 // Givens least squares for min || beta e1 - H y ||, H (m+1) x m (ld m+1),
@@ -372,11 +414,24 @@ struct Amen {
   bool mixed_local = false;   // FP32 operator inside the local GMRES cycles
   double global_check = 0.0;  // > 0: check the FP64 global residual once max local <= global_check * tol
   bool stall_exit = false;    // stop when two sweeps in a row fail to halve the best max local residual
+  // correction solves of the outer refinement: stop as soon as the global
+  // residual of outer_u + x for the system outer_A u = outer_f is <= outer_tol
+  const qtt_tensor* outer_A = nullptr;
+  const qtt_tensor* outer_u = nullptr;
+  const qtt_tensor* outer_f = nullptr;
+  double outer_tol = 0.0;
   // interfaces: PhiR[k] (bond k), k = 0..D
   std::vector<DBuf<T>> XAX_R, XY_R, ZAX_R, ZY_R;
   DBuf<T> XAX_L, XY_L, ZAX_L, ZY_L, XAX_Ln, XY_Ln, ZAX_Ln, ZY_Ln;
   double* dscal;   // device scratch scalars
   qtt_solve_info* info;
+  // FP32 copies of the current core's local operator (mixed precision),
+  // made once per core and shared by the Krylov cycles and the truncation
+  struct Op32 {
+    float* PL = nullptr;
+    float* Ak = nullptr;
+    float* PR = nullptr;
+  } op32;
 
   Amen(cudaStream_t st, Arena& a) : s(st), ar(a) {}
 
@@ -498,15 +553,21 @@ struct Amen {
     const U* PR = reinterpret_cast<const U*>(PhiR);
     const U* Ak = reinterpret_cast<const U*>(A->core[k]);
     if (sizeof(U) != sizeof(T)) {
-      U* a = sc.alloc<U>((size_t)r0 * R0 * r0);
-      convert<T, U>(s, PhiL, a, (size_t)r0 * R0 * r0);
-      U* b = sc.alloc<U>((size_t)r1 * R1 * r1);
-      convert<T, U>(s, PhiR, b, (size_t)r1 * R1 * r1);
-      U* c = sc.alloc<U>((size_t)R0 * n * n * R1);
-      convert<T, U>(s, (const T*)A->core[k], c, (size_t)R0 * n * n * R1);
-      PL = a;
-      PR = b;
-      Ak = c;
+      if (op32.PL) {   // converted once for this core
+        PL = reinterpret_cast<const U*>(op32.PL);
+        PR = reinterpret_cast<const U*>(op32.PR);
+        Ak = reinterpret_cast<const U*>(op32.Ak);
+      } else {
+        U* a = sc.alloc<U>((size_t)r0 * R0 * r0);
+        convert<T, U>(s, PhiL, a, (size_t)r0 * R0 * r0);
+        U* b = sc.alloc<U>((size_t)r1 * R1 * r1);
+        convert<T, U>(s, PhiR, b, (size_t)r1 * R1 * r1);
+        U* c = sc.alloc<U>((size_t)R0 * n * n * R1);
+        convert<T, U>(s, (const T*)A->core[k], c, (size_t)R0 * n * n * R1);
+        PL = a;
+        PR = b;
+        Ak = c;
+      }
     }
     U* V = sc.alloc<U>((size_t)N * (m + 1));
     U* w = sc.alloc<U>(N);
@@ -582,15 +643,21 @@ struct Amen {
     const U* PR = reinterpret_cast<const U*>(PhiR);
     const U* Ak = reinterpret_cast<const U*>(A->core[k]);
     if (sizeof(U) != sizeof(T)) {
-      U* a = sc.alloc<U>((size_t)r0 * R0 * r0);
-      convert<T, U>(s, PhiL, a, (size_t)r0 * R0 * r0);
-      U* b = sc.alloc<U>((size_t)r1 * R1 * r1);
-      convert<T, U>(s, PhiR, b, (size_t)r1 * R1 * r1);
-      U* c = sc.alloc<U>((size_t)R0 * n * n * R1);
-      convert<T, U>(s, (const T*)A->core[k], c, (size_t)R0 * n * n * R1);
-      PL = a;
-      PR = b;
-      Ak = c;
+      if (op32.PL) {   // converted once for this core
+        PL = reinterpret_cast<const U*>(op32.PL);
+        PR = reinterpret_cast<const U*>(op32.PR);
+        Ak = reinterpret_cast<const U*>(op32.Ak);
+      } else {
+        U* a = sc.alloc<U>((size_t)r0 * R0 * r0);
+        convert<T, U>(s, PhiL, a, (size_t)r0 * R0 * r0);
+        U* b = sc.alloc<U>((size_t)r1 * R1 * r1);
+        convert<T, U>(s, PhiR, b, (size_t)r1 * R1 * r1);
+        U* c = sc.alloc<U>((size_t)R0 * n * n * R1);
+        convert<T, U>(s, (const T*)A->core[k], c, (size_t)R0 * n * n * R1);
+        PL = a;
+        PR = b;
+        Ak = c;
+      }
     }
     U* d = sc.alloc<U>(N);
     U* r = sc.alloc<U>(N);
@@ -705,14 +772,30 @@ struct Amen {
     return rel;
   }
 
-  double local_residual(int k, const T* PhiL, int r0, const T* PhiR, int r1, const T* g, double gn, const T* xk) {
+  double local_residual(int k, const T* PhiL, int r0, const T* PhiR, int r1, const T* g, double gn, const T* xk,
+                        T* keep = nullptr) {
     const int N = r0 * A->n[k] * r1;
     Arena sc(s);
-    T* w = sc.alloc<T>(N);
+    T* w = keep ? keep : sc.alloc<T>(N);
     local_apply(PhiL, r0, r0, k, PhiR, r1, r1, xk, w, sc);
-    axpby<T>(s, N, T(-1), g, T(1), w);
+    axpby<T>(s, N, T(-1), g, T(1), w);      // w = B x - g
     double rn = host_norm(w, N);
     return gn > 0 ? rn / gn : rn;
+  }
+
+  // ||B t - w|| / gn with t applied in FP32 (the FP32 operator of op32) and
+  // w = B x_sol - g in FP64: the local residual of x_sol - t.
+  double tail_residual32(int k, int r0, int r1, const float* t32, const T* w, double gn, Arena& sc) {
+    const int n = A->n[k], N = r0 * n * r1;
+    float* bt = sc.alloc<float>(N);
+    apply_local<float>(s, sc, op32.PL, r0, r0, op32.Ak, rA(k), n, rA(k + 1), op32.PR, r1, r1, t32, bt);
+    QTT_CUDA(cudaMemsetAsync(dscal, 0, sizeof(double), s));
+    diff_sumsq_kernel<T><<<std::min(grid_for(N), 2 * num_sms()), 256, 0, s>>>(bt, w, N, dscal);
+    QTT_CHECK_LAUNCH();
+    double h;
+    QTT_CUDA(cudaMemcpyAsync(&h, dscal, sizeof(double), cudaMemcpyDeviceToHost, s));
+    QTT_CUDA(cudaStreamSynchronize(s));
+    return gn > 0 ? std::sqrt(h) / gn : std::sqrt(h);
   }
 
   void ensure_core(qtt_tensor* t, int k, size_t elems) { tensor_reserve(t, k, elems, s); }
@@ -767,6 +850,15 @@ struct Amen {
           lu_solve<T>(s, sc, N, Bm, N, sol, N, 1, dinfo);
         } else {
           QTT_CUDA(cudaMemcpyAsync(sol, xk, sizeof(T) * N, cudaMemcpyDeviceToDevice, s));
+          if (mixed_local && sizeof(T) == 8) {
+            const int R0 = rA(k), R1 = rA(k + 1);
+            op32.PL = sc.alloc<float>((size_t)r0 * R0 * r0);
+            convert<T, float>(s, XAX_L.p, op32.PL, (size_t)r0 * R0 * r0);
+            op32.PR = sc.alloc<float>((size_t)r1 * R1 * r1);
+            convert<T, float>(s, PhiR, op32.PR, (size_t)r1 * R1 * r1);
+            op32.Ak = sc.alloc<float>((size_t)R0 * n * n * R1);
+            convert<T, float>(s, (const T*)A->core[k], op32.Ak, (size_t)R0 * n * n * R1);
+          }
           if (A->sym) {
             if (mixed_local && sizeof(T) == 8) cg<float>(k, XAX_L.p, r0, PhiR, r1, g, gn, sol, delta);
             else cg<T>(k, XAX_L.p, r0, PhiR, r1, g, gn, sol, delta);
@@ -776,9 +868,11 @@ struct Amen {
         if (info) info->local_solves += 1;
         if (k == D - 1) {
           QTT_CUDA(cudaMemcpyAsync(xk, sol, sizeof(T) * N, cudaMemcpyDeviceToDevice, s));
+          op32 = Op32{};
           break;
         }
-        const double res_sol = local_residual(k, XAX_L.p, r0, PhiR, r1, g, gn, sol);
+        T* wsol = sc.alloc<T>(N);
+        const double res_sol = local_residual(k, XAX_L.p, r0, PhiR, r1, g, gn, sol, wsol);
         // SVD of the left unfolding (r0 n) x r1
         const int rows = r0 * n, kk = std::min(rows, r1);
         T* Acp = sc.alloc<T>(N);
@@ -794,11 +888,31 @@ struct Amen {
         T* SV = sc.alloc<T>((size_t)kk * r1);
         scale_rows_kernel<T><<<grid_for((long long)kk * r1), 256, 0, s>>>(kk, r1, Vt, kk, S, SV, kk);
         QTT_CHECK_LAUNCH();
-        while (lo < hi) {
-          int mid = (lo + hi) / 2;
-          gemm<T>(s, false, false, rows, r1, mid, T(1), U, rows, 0, SV, kk, 0, T(0), cand, rows, 0);
-          if (local_residual(k, XAX_L.p, r0, PhiR, r1, g, gn, cand) <= thr) hi = mid;
-          else lo = mid + 1;
+        if (op32.PL) {
+          // mixed precision: the residual of x_sol - tail_m is w_sol - B tail_m
+          // with w_sol = B x_sol - g exact in FP64 and only the small tail
+          // applied in FP32 (an FP32 error relative to B tail_m moves the
+          // chosen rank by one at most; the FP64 global check decides)
+          float* U32 = sc.alloc<float>((size_t)rows * kk);
+          float* SV32 = sc.alloc<float>((size_t)kk * r1);
+          float* tail = sc.alloc<float>(N);
+          convert<T, float>(s, U, U32, (size_t)rows * kk);
+          convert<T, float>(s, SV, SV32, (size_t)kk * r1);
+          while (lo < hi) {
+            int mid = (lo + hi) / 2;
+            Arena bs(s);
+            gemm<float>(s, false, false, rows, r1, kk - mid, 1.f, U32 + (size_t)rows * mid, rows, 0, SV32 + mid, kk,
+                        0, 0.f, tail, rows, 0);
+            if (tail_residual32(k, r0, r1, tail, wsol, gn, bs) <= thr) hi = mid;
+            else lo = mid + 1;
+          }
+        } else {
+          while (lo < hi) {
+            int mid = (lo + hi) / 2;
+            gemm<T>(s, false, false, rows, r1, mid, T(1), U, rows, 0, SV, kk, 0, T(0), cand, rows, 0);
+            if (local_residual(k, XAX_L.p, r0, PhiR, r1, g, gn, cand) <= thr) hi = mid;
+            else lo = mid + 1;
+          }
         }
         int rk = hi;
         if (max_rank > 0) rk = std::min(rk, std::max(1, max_rank - kick));
@@ -864,6 +978,7 @@ struct Amen {
         XY_L.swap(XY_Ln);
         ZAX_L.swap(ZAX_Ln);
         ZY_L.swap(ZY_Ln);
+        op32 = Op32{};
       }
       if (info) {
         info->sweeps += 1;
@@ -879,6 +994,17 @@ struct Amen {
       if (max_res <= tloc) {
         status = QTT_OK;
         break;
+      }
+      // a correction good enough for the outer system ends its solve early
+      // (affordable when the global residual is applied in full format)
+      if (outer_u && sweep >= 2 && has_fe_operator(outer_A)) {
+        const double rel = timed_residual64(s, outer_A, outer_u, outer_f, info, x);
+        if (verbose)
+          fprintf(stderr, "[qtt_solve] sweep %d: outer residual with this correction %.3e\n", sweep + 1, rel);
+        if (rel <= outer_tol) {
+          status = QTT_OK;
+          break;
+        }
       }
       // Near the tolerance the local residuals can hover above it while the
       // global one is already below (the local ones are projections of the
@@ -942,10 +1068,16 @@ Tptr default_z0(cudaStream_t s, const qtt_tensor* f, int rho, int prec) {
   return z;
 }
 
+struct OuterCheck {
+  const qtt_tensor* u = nullptr;
+  const qtt_tensor* f = nullptr;
+  double tol = 0.0;
+};
+
 template <typename T>
 int amen_run(cudaStream_t s, const qtt_tensor* K, const qtt_tensor* f, qtt_tensor* x, qtt_tensor* z, double tol,
              const qtt_solve_opts& o, qtt_solve_info* info, bool mixed_local = false, bool stall_exit = false,
-             double global_check = 30.0) {
+             double global_check = 30.0, OuterCheck outer = OuterCheck{}) {
   Arena ar(s);
   Amen<T> am(s, ar);
   am.A = K;
@@ -965,6 +1097,12 @@ int amen_run(cudaStream_t s, const qtt_tensor* K, const qtt_tensor* f, qtt_tenso
   am.mixed_local = mixed_local;
   am.global_check = global_check;
   am.stall_exit = stall_exit;
+  if (outer.u) {
+    am.outer_A = K;
+    am.outer_u = outer.u;
+    am.outer_f = outer.f;
+    am.outer_tol = outer.tol;
+  }
   am.dscal = ar.alloc<double>(4);
   int rc = am.run();
   QTT_CUDA(cudaStreamSynchronize(s));
@@ -1095,7 +1233,11 @@ int solve(const qtt_tensor* K, const qtt_tensor* f, const qtt_tensor* x0, const 
       // the correction is noise-like and of higher rank than u: enrich twice as fast
       auto d = default_x0(s, f, QTT_F64);
       auto zd = default_z0(s, f, 2 * rho, QTT_F64);
-      amen_run<double>(s, K, r.get(), d.get(), zd.get(), inner, o, inf, mixed, true, 0.0);
+      OuterCheck oc;
+      oc.u = u.get();
+      oc.f = f;
+      oc.tol = o.tol;
+      amen_run<double>(s, K, r.get(), d.get(), zd.get(), inner, o, inf, mixed, true, 0.0, oc);
       // u + d is rounded only at the level of FP64 noise: K amplifies the
       // high-frequency part of a truncation error by up to its condition
       // number (~4^L), so truncating u + d at anything near tol would

@@ -560,6 +560,15 @@ void assemble(const qtt_problem* P, qtt_tensor** Kout, qtt_tensor** fout, cudaSt
   // one patch: K = M K0 M + (I - M) with K0 symmetric is symmetric; the
   // concatenated multi-patch system is not (Section 3.6 reading)
   K->sym = (q == 1) ? 1 : 0;
+  auto fe = std::make_shared<FeOperator>();
+  fe->L = L;
+  fe->q = q;
+  fe->patch_xy.assign(P->patch_xy, P->patch_xy + 2 * q);
+  fe->bc.assign(P->bc, P->bc + 4 * q);
+  fe->E = P->E;
+  fe->nu = P->nu;
+  fe->gamma = gamma;
+  K->fe = fe;
   *Kout = K.release();
   *fout = f.release();
 }

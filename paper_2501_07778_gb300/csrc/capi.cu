@@ -122,6 +122,7 @@ int qtt_round(qtt_tensor* x, double tol, int max_rank, void* stream) {
   QTT_API_BEGIN
   QTT_REQUIRE(x, "qtt_round: null tensor");
   QTT_REQUIRE(tol >= 0.0, "qtt_round: negative tolerance");
+  x->fe.reset();   // rounded in place: no longer the assembled operator exactly
   cudaStream_t s = as_stream(stream);
   StreamScope scope_(s);
   Arena ar(s);

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <cstdio>
+#include <memory>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -108,6 +109,18 @@ class Arena {
 
 }  // namespace qtt
 
+namespace qtt {
+// The finite-element problem an assembled stiffness MPO represents (set by
+// qtt_assemble_stiffness, dropped when the MPO is changed in place): enough
+// to apply the same operator as a stencil in full format (fe_residual.cu).
+struct FeOperator {
+  int L = 0, q = 0;
+  std::vector<int> patch_xy;   // 2q integer patch offsets
+  std::vector<int> bc;         // 4q side flags (left, right, bottom, top)
+  double E = 0, nu = 0, gamma = 0;
+};
+}  // namespace qtt
+
 // ---------------------------------------------------------------------------
 // Tensor object (opaque to C callers).
 // ---------------------------------------------------------------------------
@@ -122,6 +135,7 @@ struct qtt_tensor {
   size_t cap[QTT_MAX_CORES] = {0};   // elements allocated per core
   cudaStream_t stream = nullptr;     // stream the cores were allocated on (stream-ordered frees)
   int sym = 0;                       // MPO known to be symmetric (set by the assembly for q = 1)
+  std::shared_ptr<const qtt::FeOperator> fe;   // assembled problem (stiffness MPOs only)
 };
 
 namespace qtt {

@@ -103,6 +103,7 @@ void tensor_reserve(qtt_tensor* t, int k, size_t elems, cudaStream_t s) {
 qtt_tensor* tensor_clone(const qtt_tensor* src, int prec, cudaStream_t s) {
   qtt_tensor* t = tensor_alloc(src->d, src->n, src->m, src->r, prec, src->is_matrix);
   t->sym = src->sym;
+  if (src->prec == prec) t->fe = src->fe;
   for (int k = 0; k < src->d; ++k) {
     size_t e = core_elems(src, k);
     if (src->prec == prec) {
