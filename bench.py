@@ -53,7 +53,7 @@ MAX_SWEEPS = 24
 KICK_RANK = 8
 _T0 = time.perf_counter()
 CLASSES = {0: "gemm_f64", 1: "gemm_f32", 2: "core_product", 3: "qr_panel", 4: "jacobi_svd", 5: "lu_panel",
-           6: "permute", 7: "to_full", 8: "pcg_f32", 9: "jacobi_f32"}
+           6: "permute", 7: "to_full", 8: "pcg_f32", 9: "jacobi_f32", 10: "tc_gemm_tf32x3"}
 
 
 def log(msg: str):
@@ -362,6 +362,11 @@ def roofline_of(prof, peaks, sms):
     if dom in ("gemm_f64", "qr_panel", "jacobi_svd", "lu_panel"):
         bound, unit, peak = "alu", "TFLOP/s", peaks.get("fp64_tflops")
         src = "FP64 FMA rate measured live by the library's all-SM FMA-chain kernel (qtt_measure_fma_peak)"
+        achieved = fl / 1e12 / sec if sec > 0 else 0.0
+    elif dom == "tc_gemm_tf32x3":
+        bound, unit, peak = "tensor", "TFLOP/s", peaks.get("bf16_tflops", 1892.4) / 2.0 / 3.0
+        src = ("3xTF32 on tcgen05: MEASURED_PEAKS bf16_tflops x 1/2 (TF32 vs BF16 dense rate) x 1/3 (three MMAs "
+               "per product)")
         achieved = fl / 1e12 / sec if sec > 0 else 0.0
     elif dom in ("gemm_f32", "pcg_f32", "jacobi_f32"):
         bound, unit, peak = "alu", "TFLOP/s", peaks.get("fp32_tflops")

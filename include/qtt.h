@@ -338,6 +338,22 @@ int qtt_ws_to_tensor(const float* out_row, int d, const int* modes, int r, doubl
                      qtt_tensor** x, void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Dense building block                                                      */
+/* ------------------------------------------------------------------------ */
+
+/* D = A B^T in FP32 accuracy on the tcgen05 tensor cores (3xTF32: every
+ * operand split into a TF32 pair hi + lo, products hi hi + hi lo + lo hi
+ * accumulated in FP32; the dense contractions of the FP32 local operator use
+ * the same kernel).  A: M x K, element (m, k) at A[m lda + k]; B: N x K, element
+ * (n, k) at B[n ldb + k]; D: M x N column-major, D[m + n ldd].  All DEVICE
+ * float pointers owned by the caller; the call takes device scratch for the
+ * split operands and synchronises the stream.  QTT_EINVAL on bad sizes or a
+ * device other than sm_103; QTT_ETIMEOUT if a bounded wait in the kernel gave
+ * up (the context stays usable). */
+int qtt_gemm_tf32x3(int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* D, int ldd,
+                    void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* Diagnostics (not part of the method)                                      */
 /* ------------------------------------------------------------------------ */
 
@@ -361,7 +377,7 @@ int qtt_measure_fma_peak(int prec, double* tflops, void* stream);
  * 2 MPO x MPS core product, 3 Householder panel, 4 Jacobi SVD, 5 LU panel,
  * 6 permutation, 7 full expansion, 8 persistent FP32 local CG (one launch runs
  * all iterations of a CG cycle), 9 FP32 Jacobi sweeps of the mixed-precision
- * SVD (class 4 then holds the FP64 sweeps). */
+ * SVD (class 4 then holds the FP64 sweeps), 10 tensor-core 3xTF32 GEMM. */
 int qtt_profile_enable(int on);
 
 /* Sum of event-timed milliseconds, algorithmic flops and bytes, and launch

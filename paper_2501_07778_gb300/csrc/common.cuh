@@ -49,7 +49,7 @@ void count_alloc();
 // Per-kernel-class CUDA-event timing, active after qtt_profile_enable(1).
 enum ProfClass { PROF_GEMM_F64 = 0, PROF_GEMM_F32 = 1, PROF_CORE_PRODUCT = 2, PROF_QR_PANEL = 3, PROF_JACOBI = 4,
                  PROF_LU_PANEL = 5, PROF_PERMUTE = 6, PROF_TO_FULL = 7, PROF_PCG = 8, PROF_JACOBI_F32 = 9,
-                 PROF_NCLASS = 10 };
+                 PROF_TC_GEMM = 10, PROF_NCLASS = 11 };
 struct ProfToken {
   int cls;
   cudaEvent_t ev;

@@ -17,6 +17,7 @@ namespace qtt {
 namespace {
 
 constexpr int NB = 32;         // panel width
+constexpr size_t kJacobiSmem = 200 * 1024;   // dynamic shared memory of the in-smem Jacobi sweeps
 constexpr int PT = 1024;       // panel kernel threads
 
 __device__ __forceinline__ double wsum(double v) {
@@ -140,10 +141,42 @@ inline int grid_for(long long n) { return grid_for_n(n, 16); }
 // ---------------------------------------------------------------------------
 // One-sided Jacobi on W (m x n, ldw) accumulating V (n x n, ldv); single CTA.
 // ---------------------------------------------------------------------------
+template <typename T, typename Acc>
+__device__ int jacobi_body(int m, int n, T* W, int ldw, T* Vm, int ldv, int max_sweeps, int* rotated_flag);
+
 template <typename T, typename Acc = double>
 __global__ void __launch_bounds__(1024) jacobi_kernel(int m, int n, T* W, int ldw, T* Vm, int ldv, int max_sweeps,
                                                       int* sweeps_out) {
   __shared__ int rotated;
+  const int sweep = jacobi_body<T, Acc>(m, n, W, ldw, Vm, ldv, max_sweeps, &rotated);
+  if (threadIdx.x == 0 && sweeps_out) *sweeps_out = sweep;
+}
+
+// The same sweeps with W (and V when both fit) held in shared memory for the
+// whole factorisation: every round reads and rewrites two columns of each
+// pair, which from global memory costs an L2 round trip per access.
+template <typename T, typename Acc = double>
+__global__ void __launch_bounds__(1024) jacobi_smem_kernel(int m, int n, T* W, int ldw, T* Vm, int ldv, int max_sweeps,
+                                                           int v_in_smem) {
+  extern __shared__ __align__(16) unsigned char jsm[];
+  __shared__ int rotated;
+  T* Ws = reinterpret_cast<T*>(jsm);
+  T* Vs = v_in_smem ? Ws + (size_t)m * n : Vm;
+  const int ldvs = v_in_smem ? n : ldv;
+  for (long long t = threadIdx.x; t < (long long)m * n; t += blockDim.x) Ws[t] = W[(t % m) + (t / m) * (long long)ldw];
+  if (v_in_smem)
+    for (long long t = threadIdx.x; t < (long long)n * n; t += blockDim.x) Vs[t] = Vm[(t % n) + (t / n) * (long long)ldv];
+  __syncthreads();
+  jacobi_body<T, Acc>(m, n, Ws, m, Vs, ldvs, max_sweeps, &rotated);
+  __syncthreads();
+  for (long long t = threadIdx.x; t < (long long)m * n; t += blockDim.x) W[(t % m) + (t / m) * (long long)ldw] = Ws[t];
+  if (v_in_smem)
+    for (long long t = threadIdx.x; t < (long long)n * n; t += blockDim.x) Vm[(t % n) + (t / n) * (long long)ldv] = Vs[t];
+}
+
+template <typename T, typename Acc>
+__device__ int jacobi_body(int m, int n, T* W, int ldw, T* Vm, int ldv, int max_sweeps, int* rotated_flag) {
+  int& rotated = *rotated_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int np = n + (n & 1);                  // even number of positions
   const Acc tol = (Acc)(1e-15 * (double)(m > 1 ? m : 1));
@@ -200,7 +233,7 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int m, int n, T* W, int ld
     if (!rotated) break;
     __syncthreads();
   }
-  if (threadIdx.x == 0 && sweeps_out) *sweeps_out = sweep;
+  return sweep;
 }
 
 // ---------------------------------------------------------------------------
@@ -548,7 +581,19 @@ void svd(cudaStream_t s, Arena& ar, int m, int n, T* A, int lda, T* U, int ldu, 
     set_identity_kernel<float><<<grid_for((long long)n * n), 256, 0, s>>>(V32, n, n, n);
     QTT_CHECK_LAUNCH();
     ProfToken pf = prof_begin(PROF_JACOBI_F32, s);
-    jacobi_kernel<float, float><<<1, 1024, 0, s>>>(k, n, R32, k, V32, n, 40, nullptr);
+    const size_t wbytes = sizeof(float) * (size_t)k * n, vbytes = sizeof(float) * (size_t)n * n;
+    if (wbytes <= kJacobiSmem) {
+      static bool attr = false;
+      if (!attr) {
+        QTT_CUDA(cudaFuncSetAttribute(jacobi_smem_kernel<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kJacobiSmem));
+        attr = true;
+      }
+      const int vin = (wbytes + vbytes <= kJacobiSmem) ? 1 : 0;
+      jacobi_smem_kernel<float, float><<<1, 1024, wbytes + (vin ? vbytes : 0), s>>>(k, n, R32, k, V32, n, 40, vin);
+    } else {
+      jacobi_kernel<float, float><<<1, 1024, 0, s>>>(k, n, R32, k, V32, n, 40, nullptr);
+    }
     QTT_CHECK_LAUNCH();
     if (pf.ev) prof_end(pf, s, 0.5 * n * (n - 1) * (6.0 * k + 12.0 * k + 12.0 * n), 4.0 * 2.0 * (k + n) * n);
     T* V0 = ar.alloc<T>((size_t)n * n);
