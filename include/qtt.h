@@ -220,6 +220,10 @@ typedef struct {
   double inner_tol;       /* relative tolerance of each refinement's correction
                              solve (<= 0: 1e-3) */
   int verbose;            /* print per-sweep progress to stderr */
+  int tensor_cores;       /* QTT_MIXED: >= 0 runs the FP32 local operator of the
+                             Krylov iterations at ranks >= 32 as tcgen05 3xTF32
+                             GEMMs (sm_103); < 0 keeps it on the FP32 SIMT
+                             pipes */
 } qtt_solve_opts;
 
 typedef struct {
@@ -347,7 +351,9 @@ int qtt_ws_to_tensor(const float* out_row, int d, const int* modes, int r, doubl
  * the same kernel).  A: M x K, element (m, k) at A[m lda + k]; B: N x K, element
  * (n, k) at B[n ldb + k]; D: M x N column-major, D[m + n ldd].  All DEVICE
  * float pointers owned by the caller; the call takes device scratch for the
- * split operands and synchronises the stream.  QTT_EINVAL on bad sizes or a
+ * split operands and synchronises the stream.  When the output tiles cannot
+ * fill the SMs the K loop is split over CTAs and accumulated atomically into
+ * D (zeroed first), so the summation order is not fixed.  QTT_EINVAL on bad sizes or a
  * device other than sm_103; QTT_ETIMEOUT if a bounded wait in the kernel gave
  * up (the context stays usable). */
 int qtt_gemm_tf32x3(int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* D, int ldd,

@@ -234,9 +234,10 @@ def qtt_assemble_stiffness(prob, tol: float = 0.0, stream=None):
 
 
 def solve_opts(tol=1e-8, max_rank=0, kick_rank=0, max_sweeps=0, local_direct_max=0, local_restart=0,
-               local_max_cycles=0, precision=QTT_F64, refine_max=0, inner_tol=0.0, verbose=0) -> QttSolveOpts:
+               local_max_cycles=0, precision=QTT_F64, refine_max=0, inner_tol=0.0, verbose=0,
+               tensor_cores=0) -> QttSolveOpts:
     return QttSolveOpts(tol, max_rank, kick_rank, max_sweeps, local_direct_max, local_restart, local_max_cycles,
-                        precision, refine_max, inner_tol, verbose)
+                        precision, refine_max, inner_tol, verbose, tensor_cores)
 
 
 def qtt_solve_batched(Ks: List[QTT], fs: List[QTT], x0s: Optional[List[Optional[QTT]]] = None, nworkers: int = 0,

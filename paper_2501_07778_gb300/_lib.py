@@ -33,7 +33,8 @@ class QttProblem(C.Structure):
 class QttSolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_rank", C.c_int), ("kick_rank", C.c_int), ("max_sweeps", C.c_int),
                 ("local_direct_max", C.c_int), ("local_restart", C.c_int), ("local_max_cycles", C.c_int),
-                ("precision", C.c_int), ("refine_max", C.c_int), ("inner_tol", C.c_double), ("verbose", C.c_int)]
+                ("precision", C.c_int), ("refine_max", C.c_int), ("inner_tol", C.c_double), ("verbose", C.c_int),
+                ("tensor_cores", C.c_int)]
 
 
 class QttSolveInfo(C.Structure):

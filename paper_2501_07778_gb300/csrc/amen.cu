@@ -29,6 +29,7 @@
 
 #include "common.cuh"
 #include "contract.cuh"
+#include "tc_gemm.cuh"
 #include "tt_ops.cuh"
 
 namespace qtt {
@@ -398,6 +399,98 @@ void apply_local(cudaStream_t s, Arena& sc, const U* PhiL, int ra, int rc, const
 }
 
 // ---------------------------------------------------------------------------
+// The FP32 local operator B p = Phi_L K_k Phi_R p on the tensor cores: the
+// three contractions of apply_local as K-major 3xTF32 GEMMs (tc_gemm.cu),
+//   t1[(c,b); (j,B)] = sum_d   p[(c,j); d]       Phi_R[(b,B); d]
+//   t2[(i,b); (A,c)] = sum_jB  t1[(c,b); (j,B)]  K_k[(A,i); (j,B)]
+//   q[a, i, b]       = sum_Ac  Phi_L[a; (A,c)]   t2[(i,b); (A,c)]
+// where every epilogue writes its output directly in the K-major TF32-pair
+// layout the next GEMM reads; the fixed factors are packed once per local
+// solve, p once per application (the last GEMM splits its long K loop).
+// ---------------------------------------------------------------------------
+inline int pad4(int x) { return (x + 3) / 4 * 4; }
+
+inline TcIdxMap idx1(int n0, long long s0) {
+  TcIdxMap m{};
+  m.cnt = 1;
+  m.n[0] = n0;
+  m.s[0] = s0;
+  return m;
+}
+inline TcIdxMap idx2(int n0, long long s0, int n1, long long s1) {
+  TcIdxMap m{};
+  m.cnt = 2;
+  m.n[0] = n0;
+  m.s[0] = s0;
+  m.n[1] = n1;
+  m.s[1] = s1;
+  return m;
+}
+
+struct TcLocalOp {
+  int r0 = 0, n = 0, r1 = 0, R0 = 0, R1 = 0, ld1 = 0, ld2 = 0, ld3 = 0;
+  float *pTh = nullptr, *pTl = nullptr;
+  TcGemmPlan g1, g2, g3;
+
+  // PL (r0, R0, r0), Ak (R0, n, n, R1), PR (r1, R1, r1): FP32, column-major;
+  // q: the output vector (r0, n, r1)
+  void build(cudaStream_t s, Arena& ar, const float* PL, const float* Ak, const float* PR, int r0_, int n_, int r1_,
+             int R0_, int R1_, float* q) {
+    r0 = r0_, n = n_, r1 = r1_, R0 = R0_, R1 = R1_;
+    ld1 = pad4(r1);
+    ld2 = pad4(n * R1);
+    ld3 = pad4(R0 * r0);
+    const int M1 = r0 * n, N1 = r1 * R1, M2 = r0 * r1, N2 = R0 * n, M3 = r0, N3 = n * r1;
+    pTh = ar.alloc<float>((size_t)M1 * ld1);
+    pTl = ar.alloc<float>((size_t)M1 * ld1);
+    float* PRh = ar.alloc<float>((size_t)N1 * ld1);
+    float* PRl = ar.alloc<float>((size_t)N1 * ld1);
+    float* t1h = ar.alloc<float>((size_t)M2 * ld2);
+    float* t1l = ar.alloc<float>((size_t)M2 * ld2);
+    float* Kh = ar.alloc<float>((size_t)N2 * ld2);
+    float* Kl = ar.alloc<float>((size_t)N2 * ld2);
+    float* PLh = ar.alloc<float>((size_t)M3 * ld3);
+    float* PLl = ar.alloc<float>((size_t)M3 * ld3);
+    float* t2h = ar.alloc<float>((size_t)N3 * ld3);
+    float* t2l = ar.alloc<float>((size_t)N3 * ld3);
+    // fixed factors: Phi_R[(b,B); d], K[(A,i); (j,B)], Phi_L[a; (A,c)]
+    tc_pack(s, PR, N1, r1, ld1, idx2(r1, 1, R1, r1), idx1(r1, (long long)r1 * R1), PRh, PRl);
+    tc_pack(s, Ak, N2, n * R1, ld2, idx2(R0, 1, n, R0), idx2(n, (long long)R0 * n, R1, (long long)R0 * n * n), Kh, Kl);
+    tc_pack(s, PL, M3, R0 * r0, ld3, idx1(r0, 1), idx2(R0, r0, r0, (long long)r0 * R0), PLh, PLl);
+    TcEpilogue e1{};
+    e1.om = idx2(r0, ld2, n, 1);                                   // (c, j) -> row c + r0 b, column j + n B
+    e1.on = idx2(r1, (long long)r0 * ld2, R1, n);
+    e1.out = t1h;
+    e1.lo = t1l;
+    tc_plan(g1, M1, N1, r1, pTh, pTl, ld1, PRh, PRl, ld1, e1, 1);
+    TcEpilogue e2{};
+    e2.om = idx2(r0, R0, r1, (long long)n * ld3);                  // (c, b) -> row i + n b, column A + R0 c
+    e2.on = idx2(R0, 1, n, ld3);
+    e2.out = t2h;
+    e2.lo = t2l;
+    tc_plan(g2, M2, N2, n * R1, t1h, t1l, ld2, Kh, Kl, ld2, e2, 1);
+    TcEpilogue e3{};
+    e3.om = idx1(r0, 1);                                           // q[a, i, b] at a + r0 (i + n b)
+    e3.on = idx2(n, r0, r1, (long long)r0 * n);
+    e3.out = q;
+    e3.lo = nullptr;
+    const long long tiles3 = (long long)((M3 + 127) / 128) * ((N3 + 127) / 128);
+    const int want = (int)std::max<long long>(1, (2LL * num_sms() + tiles3 - 1) / tiles3);
+    e3.atomic = want > 1 ? 1 : 0;
+    tc_plan(g3, M3, N3, R0 * r0, PLh, PLl, ld3, t2h, t2l, ld3, e3, want);
+  }
+
+  // q = B p (q as given to build)
+  void apply(cudaStream_t s, const float* p, int* err) {
+    tc_pack(s, p, r0 * n, r1, ld1, idx2(r0, 1, n, r0), idx1(r1, (long long)r0 * n), pTh, pTl);
+    tc_run(s, g1, err);
+    tc_run(s, g2, err);
+    if (g3.epi.atomic) QTT_CUDA(cudaMemsetAsync(g3.epi.out, 0, sizeof(float) * (size_t)r0 * n * r1, s));
+    tc_run(s, g3, err);
+  }
+};
+
+// ---------------------------------------------------------------------------
 // the solver
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -412,6 +505,8 @@ struct Amen {
   double tol;
   int max_rank, kick, max_sweeps, ndir, restart, cycles, verbose;
   bool mixed_local = false;   // FP32 operator inside the local GMRES cycles
+  bool tensor_cores = false;  // the FP32 local operator on tcgen05 (3xTF32) at ranks >= 32
+  int* tc_err = nullptr;      // device word set by a tensor-core kernel whose bounded wait gave up
   double global_check = 0.0;  // > 0: check the FP64 global residual once max local <= global_check * tol
   bool stall_exit = false;    // stop when two sweeps in a row fail to halve the best max local residual
   // correction solves of the outer refinement: stop as soon as the global
@@ -687,6 +782,12 @@ struct Amen {
       inv_diag_kernel<T, U><<<(N + 255) / 256, 256, 0, s>>>(dg, minv, N);
       QTT_CHECK_LAUNCH();
     }
+    const bool use_tc = sizeof(U) == 4 && sizeof(T) == 8 && tensor_cores && op32.PL && tc_err && r0 >= 32 &&
+                        r1 >= 32 && tc_available();
+    TcLocalOp tl;
+    if (use_tc)
+      tl.build(s, sc, reinterpret_cast<const float*>(PL), reinterpret_cast<const float*>(Ak),
+               reinterpret_cast<const float*>(PR), r0, n, r1, R0, R1, reinterpret_cast<float*>(qv));
     double rel = 1.0, prev = -1.0;
     for (int cyc = 0; cyc < cycles; ++cyc) {
       Arena it(s);
@@ -705,7 +806,26 @@ struct Amen {
       double* rr_new = sc4 + 1;
       double* pq = sc4 + 2;
       dotp<U>(s, r, p, N, rr_old);
-      if (sizeof(U) == 4 && persistent_cg_grid() > 0) {
+      if (use_tc) {
+        // every iteration on the tensor cores: B p by three 3xTF32 GEMMs,
+        // the CG scalars on the device
+        for (int j = 0; j < m; ++j) {
+          tl.apply(s, reinterpret_cast<const float*>(p), tc_err);
+          dotp<U>(s, p, qv, N, pq);
+          cg_step_kernel<U><<<grid_for(N), 256, 0, s>>>(d, r, p, qv, rr_old, pq, N);
+          QTT_CHECK_LAUNCH();
+          precond_kernel<U><<<grid_for(N), 256, 0, s>>>(z, minv, r, N);
+          QTT_CHECK_LAUNCH();
+          dotp<U>(s, r, z, N, rr_new);
+          cg_dir_kernel<U><<<grid_for(N), 256, 0, s>>>(p, z, rr_new, rr_old, N);
+          QTT_CHECK_LAUNCH();
+          std::swap(rr_old, rr_new);
+        }
+        int herr = 0;
+        QTT_CUDA(cudaMemcpyAsync(&herr, tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        QTT_CUDA(cudaStreamSynchronize(s));
+        if (herr != 0) throw QttError(QTT_ETIMEOUT, "local CG: a tensor-core kernel's bounded wait gave up");
+      } else if (sizeof(U) == 4 && persistent_cg_grid() > 0) {
         // all m iterations in one cooperative launch
         const int grid = persistent_cg_grid();
         PcgArgs pa{};
@@ -1095,6 +1215,11 @@ int amen_run(cudaStream_t s, const qtt_tensor* K, const qtt_tensor* f, qtt_tenso
   am.verbose = o.verbose;
   am.info = info;
   am.mixed_local = mixed_local;
+  am.tensor_cores = mixed_local && o.tensor_cores >= 0;
+  if (am.tensor_cores) {
+    am.tc_err = ar.alloc<int>(1);
+    QTT_CUDA(cudaMemsetAsync(am.tc_err, 0, sizeof(int), s));
+  }
   am.global_check = global_check;
   am.stall_exit = stall_exit;
   if (outer.u) {

@@ -133,7 +133,7 @@ __device__ __forceinline__ long long map_off(const TcIdxMap& d, int idx) {
 __global__ void __launch_bounds__(128, 1)
     tf32x3_gemm_kernel(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
                        const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl, int M, int N,
-                       int K, TcEpilogue epi, int* err) {
+                       int K, int kb_per, TcEpilogue epi, int* err) {
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;                 // 1024-byte aligned tiles
@@ -142,7 +142,8 @@ __global__ void __launch_bounds__(128, 1)
   volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(gbase + STAGES * STAGE_BYTES + 8 * (2 * STAGES + 1));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-  const int nk = (K + BK - 1) / BK;
+  const int kb0 = blockIdx.z * kb_per;                        // this split's K slices
+  const int nk = min((K + BK - 1) / BK - kb0, kb_per);
   auto full = [&](int st) { return bars + 8u * st; };
   auto empty = [&](int st) { return bars + 8u * (STAGES + st); };
   const uint32_t done = bars + 8u * (2 * STAGES);
@@ -176,10 +177,11 @@ __global__ void __launch_bounds__(128, 1)
       if (!ok) break;
       const uint32_t sb = base + st * STAGE_BYTES;
       mbar_expect_tx(full(st), STAGE_BYTES);
-      tma_load_2d(sb, &tAh, full(st), kb * BK, m0);
-      tma_load_2d(sb + TILE_BYTES, &tAl, full(st), kb * BK, m0);
-      tma_load_2d(sb + 2 * TILE_BYTES, &tBh, full(st), kb * BK, n0);
-      tma_load_2d(sb + 3 * TILE_BYTES, &tBl, full(st), kb * BK, n0);
+      const int kx = (kb0 + kb) * BK;
+      tma_load_2d(sb, &tAh, full(st), kx, m0);
+      tma_load_2d(sb + TILE_BYTES, &tAl, full(st), kx, m0);
+      tma_load_2d(sb + 2 * TILE_BYTES, &tBh, full(st), kx, n0);
+      tma_load_2d(sb + 3 * TILE_BYTES, &tBl, full(st), kx, n0);
       issued = kb + 1;
     }
     // no copy may still be landing in shared memory when the CTA leaves
@@ -235,6 +237,8 @@ __global__ void __launch_bounds__(128, 1)
           const float h = tf32_round(v);
           epi.out[o] = h;
           epi.lo[o] = v - h;
+        } else if (epi.atomic) {
+          atomicAdd(epi.out + o, v);
         } else {
           epi.out[o] = v;
         }
@@ -254,6 +258,30 @@ __global__ void tf32_split_kernel(const float* __restrict__ x, float* __restrict
     const float h = tf32_round(v);
     hi[i] = h;
     lo[i] = v - h;
+  }
+}
+
+// hi/lo TF32 pairs of a rows x K K-major operand gathered from a tensor:
+// element (row, k) = src[rmap(row) + kmap(k)].  32 x 32 tiles through shared
+// memory: reads run along rows, writes along k.
+__global__ void __launch_bounds__(256) pack_pairs_kernel(const float* __restrict__ src, int rows, int K, int ld,
+                                                         TcIdxMap rmap, TcIdxMap kmap, float* __restrict__ hi,
+                                                         float* __restrict__ lo) {
+  __shared__ float tile[32][33];
+  const int r0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  for (int kk = threadIdx.y; kk < 32; kk += 8) {
+    const int r = r0 + threadIdx.x, k = k0 + kk;
+    tile[kk][threadIdx.x] = (r < rows && k < K) ? src[map_off(rmap, r) + map_off(kmap, k)] : 0.f;
+  }
+  __syncthreads();
+  for (int rr = threadIdx.y; rr < 32; rr += 8) {
+    const int r = r0 + rr, k = k0 + threadIdx.x;
+    if (r < rows && k < K) {
+      const float v = tile[threadIdx.x][rr];
+      const float h = tf32_round(v);
+      hi[(size_t)r * ld + k] = h;
+      lo[(size_t)r * ld + k] = v - h;
+    }
   }
 }
 
@@ -305,33 +333,67 @@ bool tc_available() {
   return ok == 1;
 }
 
+void tc_pack(cudaStream_t s, const float* src, int rows, int K, int ld, const TcIdxMap& rmap, const TcIdxMap& kmap,
+             float* hi, float* lo) {
+  if (rows <= 0 || K <= 0) return;
+  QTT_REQUIRE((K + 31) / 32 <= 65535, "tc_pack: K too large");
+  dim3 grid((rows + 31) / 32, (K + 31) / 32);
+  pack_pairs_kernel<<<grid, dim3(32, 8), 0, s>>>(src, rows, K, ld, rmap, kmap, hi, lo);
+  QTT_CHECK_LAUNCH();
+}
+
 void tf32_split(cudaStream_t s, const float* x, float* hi, float* lo, long long n) {
   if (n <= 0) return;
   tf32_split_kernel<<<grid_for_n(n, 8), 256, 0, s>>>(x, hi, lo, n);
   QTT_CHECK_LAUNCH();
 }
 
-void tf32x3_gemm(cudaStream_t s, int M, int N, int K, const float* Ahi, const float* Alo, int lda, const float* Bhi,
-                 const float* Blo, int ldb, const TcEpilogue& epi, int* err) {
-  if (M <= 0 || N <= 0) return;
-  QTT_REQUIRE(K >= 1, "tf32x3 gemm: K must be positive");
+void tc_plan(TcGemmPlan& p, int M, int N, int K, const float* Ahi, const float* Alo, int lda, const float* Bhi,
+             const float* Blo, int ldb, const TcEpilogue& epi, int max_splits) {
+  QTT_REQUIRE(M >= 1 && N >= 1 && K >= 1, "tf32x3 gemm: sizes must be positive");
   QTT_REQUIRE(lda % 4 == 0 && ldb % 4 == 0 && lda >= K && ldb >= K,
               "tf32x3 gemm: leading dimensions must be multiples of 4 elements (16-byte TMA strides)");
-  auto aligned16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  auto aligned16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
   QTT_REQUIRE(aligned16(Ahi) && aligned16(Alo) && aligned16(Bhi) && aligned16(Blo),
               "tf32x3 gemm: operands must start on 16-byte boundaries");
+  static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
+  const CUtensorMap maps[4] = {make_map(Ahi, M, K, lda), make_map(Alo, M, K, lda), make_map(Bhi, N, K, ldb),
+                               make_map(Blo, N, K, ldb)};
+  std::memcpy(p.maps, maps, sizeof(maps));
+  p.M = M;
+  p.N = N;
+  p.K = K;
+  const int nk = (K + BK - 1) / BK;
+  int splits = std::max(1, std::min(max_splits, nk));
+  if (epi.lo || !epi.atomic) splits = 1;
+  p.kb_per = (nk + splits - 1) / splits;
+  p.splits = (nk + p.kb_per - 1) / p.kb_per;       // every split has at least one K slice
+  p.epi = epi;
+  QTT_REQUIRE((M + BM - 1) / BM <= 2147483647 && (N + BN - 1) / BN <= 65535 && p.splits <= 65535,
+              "tf32x3 gemm: grid too large");
+}
+
+void tc_run(cudaStream_t s, const TcGemmPlan& p, int* err) {
   static std::once_flag attr;
   std::call_once(attr, [] {
     cudaFuncSetAttribute(tf32x3_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   });
-  const CUtensorMap tAh = make_map(Ahi, M, K, lda), tAl = make_map(Alo, M, K, lda);
-  const CUtensorMap tBh = make_map(Bhi, N, K, ldb), tBl = make_map(Blo, N, K, ldb);
-  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
-  QTT_REQUIRE(grid.y <= 65535, "tf32x3 gemm: N too large");
+  const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(p.maps);
+  dim3 grid((p.M + BM - 1) / BM, (p.N + BN - 1) / BN, p.splits);
   ProfToken pt = prof_begin(PROF_TC_GEMM, s);
-  tf32x3_gemm_kernel<<<grid, 128, SMEM_BYTES, s>>>(tAh, tAl, tBh, tBl, M, N, K, epi, err);
+  tf32x3_gemm_kernel<<<grid, 128, SMEM_BYTES, s>>>(m[0], m[1], m[2], m[3], p.M, p.N, p.K, p.kb_per, p.epi, err);
   QTT_CHECK_LAUNCH();
-  if (pt.ev) prof_end(pt, s, 2.0 * M * N * K, 4.0 * (2.0 * M * K + 2.0 * N * K + (epi.lo ? 2.0 : 1.0) * M * N));
+  if (pt.ev)
+    prof_end(pt, s, 2.0 * p.M * p.N * p.K,
+             4.0 * (2.0 * p.M * p.K + 2.0 * p.N * p.K + (p.epi.lo ? 2.0 : 1.0) * p.M * p.N));
+}
+
+void tf32x3_gemm(cudaStream_t s, int M, int N, int K, const float* Ahi, const float* Alo, int lda, const float* Bhi,
+                 const float* Blo, int ldb, const TcEpilogue& epi, int* err) {
+  if (M <= 0 || N <= 0) return;
+  TcGemmPlan p;
+  tc_plan(p, M, N, K, Ahi, Alo, lda, Bhi, Blo, ldb, epi, 1);
+  tc_run(s, p, err);
 }
 
 }  // namespace qtt
@@ -370,7 +432,14 @@ extern "C" int qtt_gemm_tf32x3(int M, int N, int K, const float* A, int lda, con
     epi.on.s[0] = ldd;
     epi.out = D;
     epi.lo = nullptr;
-    qtt::tf32x3_gemm(s, M, N, K, Ah, Al, ldk, Bh, Bl, ldk, epi, err);
+    // too few output tiles to fill the SMs: split K, accumulate atomically
+    const long long tiles = (long long)((M + 127) / 128) * ((N + 127) / 128);
+    const int want = (int)std::max<long long>(1, (2LL * qtt::num_sms() + tiles - 1) / tiles);
+    epi.atomic = want > 1 ? 1 : 0;
+    if (epi.atomic) QTT_CUDA(cudaMemset2DAsync(D, sizeof(float) * (size_t)ldd, 0, sizeof(float) * (size_t)M, N, s));
+    qtt::TcGemmPlan plan;
+    qtt::tc_plan(plan, M, N, K, Ah, Al, ldk, Bh, Bl, ldk, epi, want);
+    qtt::tc_run(s, plan, err);
     int herr = 0;
     QTT_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     QTT_CUDA(cudaStreamSynchronize(s));

@@ -34,3 +34,41 @@ def test_tf32x3_gemm_matches_fp64(M, N, K, pad):
     assert np.all(np.abs(D - ref) <= 1e-5 * scale + 1e-30), float(np.max(np.abs(D - ref) / scale))
     # the padding columns of D were not written
     assert np.isnan(dD.cpu().numpy()[:, M:]).all()
+
+
+def _merged_in_qtt_order(prob):
+    from oracle import fem
+    u, node_map = fem.solve_merged(prob)
+    return fem.merged_to_qtt(prob, u, node_map)
+
+
+@pytest.mark.parametrize("tensor_cores", [0, -1])
+def test_mixed_solve_with_tensor_core_local_operator(tensor_cores):
+    """QTT_MIXED with the CG forced on every core (local_direct_max = 1): with
+    tensor_cores >= 0 the FP32 local operator at ranks >= 32 runs as tcgen05
+    3xTF32 GEMMs (profile class 10 launches), otherwise on the SIMT pipes;
+    both reach the sparse direct solution."""
+    import workloads as W
+    lib = q.lib()
+    prob = W.plate_top_traction(7, 12.0, 0.28, 1.0, 1.1)
+    K, f = q.qtt_assemble_stiffness(prob)
+    ms, fl, by, n = C.c_double(), C.c_double(), C.c_double(), C.c_longlong()
+    lib.qtt_profile_read(-1, None, None, None, None)
+    lib.qtt_profile_enable(1)
+    try:
+        u, info = q.qtt_solve(K, f, tol=1e-9, precision=q.QTT_MIXED, local_direct_max=1, kick_rank=8,
+                              max_sweeps=30, tensor_cores=tensor_cores)
+        torch.cuda.synchronize()
+    finally:
+        lib.qtt_profile_enable(0)
+    lib.qtt_profile_read(10, C.byref(ms), C.byref(fl), C.byref(by), C.byref(n))
+    lib.qtt_profile_read(-1, None, None, None, None)
+    if tensor_cores >= 0:
+        assert n.value > 0, "the tensor-core GEMM did not run"
+    else:
+        assert n.value == 0
+    ug = q.qtt_to_full(u).cpu().numpy()
+    ref = _merged_in_qtt_order(prob)
+    err = np.linalg.norm(ug - ref) / np.linalg.norm(ref)
+    assert info["rc"] == 0 and info["rel_residual"] <= 1e-9, info
+    assert err <= 1e-7, (err, info)
