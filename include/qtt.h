@@ -115,12 +115,20 @@ typedef struct {
                                 diagonal of K_xx of one patch */
   double tol;                /* relative rounding tolerance of the assembled
                                 K and f (0 = 1e-13) */
+  int n_dir;                 /* separable terms of the prescribed displacement
+                                u0_c = a g(x) h(y) (Algorithm 1's u0; 0 =
+                                homogeneous Dirichlet conditions) */
+  const int* dir_terms;      /* 3 n_dir ints: (component, xkind, ykind), kinds as
+                                for the body force */
+  const double* dir_coef;    /* n_dir coefficients a */
 } qtt_problem;
 
 /* Assemble the stiffness MPO K and load MPS f of a problem in FP64 on the
  * device (Algorithm 1: 1D factors -> z-kron -> patch concatenation with
  * connectivity Pi^(mp) and penalty gamma -> component blocks -> Dirichlet
- * masks K <- M K M + (I - M), f <- M f -> rounding).  Patches are unit
+ * masks K <- M K M + (I - M), f <- M (f - K g) + g -> rounding, where
+ * g = (I - M) u0 lifts the prescribed displacement: the solution equals u0
+ * on every constrained DOF).  Patches are unit
  * squares at integer offsets; two patches share an edge or a corner exactly
  * when their offsets differ by one in one or both directions.  Creates *K and
  * *f (caller frees with qtt_free).  Errors: QTT_EINVAL for L < 1, L > 18,

@@ -207,6 +207,22 @@ def patch_load(prob, m: int) -> np.ndarray:
     return f
 
 
+def patch_dirichlet(prob, m: int) -> np.ndarray:
+    """Nodal values of the prescribed displacement u0 (Algorithm 1 input) on
+    patch m in local DOF order 2 (i + n j) + c; only constrained DOFs use
+    them."""
+    n = prob.n
+    h = 1.0 / (n - 1)
+    ox, oy = prob.patches[m]
+    x = ox + h * np.arange(n)
+    y = oy + h * np.arange(n)
+    u = np.zeros(2 * n * n)
+    for comp, coeff, kx, ky in prob.dirichlet:
+        v = coeff * np.outer(_body_factor(kx, x), _body_factor(ky, y))   # [i, j]
+        u[comp::2] += v.T.ravel()
+    return u
+
+
 # ----------------------------------------------------------------------------
 # Constraints and coincidence
 # ----------------------------------------------------------------------------
@@ -309,6 +325,7 @@ def duplicated_system(prob, masked: bool = True):
     perm_node[loc_node] = indexing.zorder(ii.ravel(), jj.ravel(), L)
     blocks = []
     f = np.zeros(N)
+    u0 = np.zeros(N)
     for m in range(q):
         Km = patch_stiffness(L, prob.E, prob.nu).tocoo()
         node_r, c_r = Km.row // 2, Km.row % 2
@@ -317,8 +334,10 @@ def duplicated_system(prob, masked: bool = True):
         cols = perm_node[node_c] + nn * m + nn * q * c_c
         blocks.append(sp.coo_matrix((Km.data, (rows, cols)), shape=(N, N)))
         fm = patch_load(prob, m)
+        um = patch_dirichlet(prob, m)
         for c in range(2):
             f[perm_node[np.arange(nn)] + nn * m + nn * q * c] += fm[c::2]
+            u0[perm_node[np.arange(nn)] + nn * m + nn * q * c] = um[c::2]
     Kblk = sp.csr_matrix((N, N))
     for b in blocks:
         Kblk = Kblk + b.tocsr()
@@ -341,9 +360,12 @@ def duplicated_system(prob, masked: bool = True):
             idx = np.nonzero((fl & bit).ravel(order="F"))[0]   # local node i + n j
             free[perm_node[idx] + nn * m + nn * q * c] = False
     if masked:
+        # lifting of the prescribed values g = (I - M) u0 (Section 3.8 masks,
+        # Algorithm 1's u0): free rows get M (f - K g), constrained rows g
+        g = np.where(free, 0.0, u0)
+        f = (f - K @ g) * free + g
         Mk = sp.diags(free.astype(float))
         K = Mk @ K @ Mk + sp.diags((~free).astype(float))
-        f = f * free
     return sp.csr_matrix(K), f, free
 
 
@@ -401,7 +423,16 @@ def solve_eliminated(K, f, free, u_fixed=None):
 
 def solve_merged(prob) -> Tuple[np.ndarray, list]:
     K, f, free, node_map = merged_system(prob)
-    return solve_eliminated(K, f, free), node_map
+    u_fixed = None
+    if prob.dirichlet:
+        u_fixed = np.zeros(K.shape[0])
+        for m in range(prob.q):
+            g = node_map[m].ravel(order="F")            # local node i + n j -> merged node
+            um = patch_dirichlet(prob, m)
+            u_fixed[2 * g] = um[0::2]
+            u_fixed[2 * g + 1] = um[1::2]
+        u_fixed = np.where(free, 0.0, u_fixed)
+    return solve_eliminated(K, f, free, u_fixed), node_map
 
 
 def merged_to_qtt(prob, u_merged: np.ndarray, node_map) -> np.ndarray:

@@ -11,7 +11,8 @@ elements of a patch are translates of one square element, so
 with Ke the 8x8 element stiffness of Section 3.4 (2x2 Gauss, plane stress),
 is sixteen shifted 2x2 block products over the node grid.  Homogeneous
 Dirichlet conditions follow the masked form of Section 3.8:
-K_bc = M K M + (I - M), f_bc = M f, M = diag(free).  The load is the
+K_bc = M K M + (I - M), f_bc = M (f - K g) + g, M = diag(free), with
+g = (I - M) u0 the prescribed values (zero for homogeneous conditions).  The load is the
 oracle's own patch load (consistent mass x intensity, edge tractions).
 Everything is plain NumPy in FP64.
 """
@@ -54,7 +55,8 @@ def masked_residual(prob, u: np.ndarray):
     free[:, :, 1] = (flags.T & 2) == 0
     free = free.reshape(-1)
     f = fem.patch_load(prob, 0)
-    fbc = np.where(free, f, 0.0)
+    g = np.where(free, 0.0, fem.patch_dirichlet(prob, 0))      # prescribed values, lifted
+    fbc = np.where(free, f - patch_apply(prob.L, prob.E, prob.nu, g), 0.0) + g
     Ku = patch_apply(prob.L, prob.E, prob.nu, np.where(free, u, 0.0))
     r = fbc - np.where(free, Ku, 0.0) - np.where(free, 0.0, u)
     return r, fbc

@@ -219,8 +219,12 @@ def make_problem_struct(prob, tol: float = 0.0):
     nt = len(prob.traction)
     tw = (C.c_int * max(1, 2 * nt))(*[v for (m, s, tx, ty) in prob.traction for v in (m, s)])
     tv = (C.c_double * max(1, 2 * nt))(*[v for (m, s, tx, ty) in prob.traction for v in (tx, ty)])
-    st = QttProblem(prob.L, q, patch, prob.E, prob.nu, bc, nb, bt, bcf, nt, tw, tv, prob.gamma, tol)
-    st._keep = (patch, bc, bt, bcf, tw, tv)
+    dirs = getattr(prob, "dirichlet", []) or []
+    nd = len(dirs)
+    dt = (C.c_int * max(1, 3 * nd))(*[v for (c, a, kx, ky) in dirs for v in (c, kx, ky)])
+    dcf = (C.c_double * max(1, nd))(*[a for (c, a, kx, ky) in dirs])
+    st = QttProblem(prob.L, q, patch, prob.E, prob.nu, bc, nb, bt, bcf, nt, tw, tv, prob.gamma, tol, nd, dt, dcf)
+    st._keep = (patch, bc, bt, bcf, tw, tv, dt, dcf)
     return st
 
 

@@ -27,7 +27,8 @@ class QttProblem(C.Structure):
                 ("E", C.c_double), ("nu", C.c_double), ("bc", C.POINTER(C.c_int)),
                 ("n_body", C.c_int), ("body_terms", C.POINTER(C.c_int)), ("body_coef", C.POINTER(C.c_double)),
                 ("n_trac", C.c_int), ("trac_where", C.POINTER(C.c_int)), ("trac_val", C.POINTER(C.c_double)),
-                ("gamma", C.c_double), ("tol", C.c_double)]
+                ("gamma", C.c_double), ("tol", C.c_double), ("n_dir", C.c_int), ("dir_terms", C.POINTER(C.c_int)),
+                ("dir_coef", C.POINTER(C.c_double))]
 
 
 class QttSolveOpts(C.Structure):

@@ -372,6 +372,13 @@ void assemble(const qtt_problem* P, qtt_tensor** Kout, qtt_tensor** fout, cudaSt
     const int* tw = P->trac_where + 2 * t;
     QTT_REQUIRE(tw[0] >= 0 && tw[0] < q && tw[1] >= 0 && tw[1] <= 3, "qtt_assemble_stiffness: bad traction");
   }
+  QTT_REQUIRE(P->n_dir >= 0 && (P->n_dir == 0 || (P->dir_terms && P->dir_coef)),
+              "qtt_assemble_stiffness: bad prescribed-displacement terms");
+  for (int t = 0; t < P->n_dir; ++t) {
+    const int* dt = P->dir_terms + 3 * t;
+    QTT_REQUIRE(dt[0] >= 0 && dt[0] <= 1 && dt[1] >= 0 && dt[1] <= 4 && dt[2] >= 0 && dt[2] <= 4,
+                "qtt_assemble_stiffness: bad prescribed-displacement term");
+  }
   const double tol = P->tol > 0 ? P->tol : 1e-13;
   const double tin = tol * 1e-2;               // intermediate sums keep more accuracy
   Arena ar(s);
@@ -447,6 +454,33 @@ void assemble(const qtt_problem* P, qtt_tensor** Kout, qtt_tensor** fout, cudaSt
       mask.push_back(std::move(acc));
     }
   }
+
+  // nodal values at x = o + h i of a separable factor (sin / cos of pi x)
+  auto factor1d = [&](int kind, double o) {
+    if (kind == V_SIN || kind == V_COS) return vec1d(s, kind, L, M_PI * o, M_PI * h);
+    return vec1d(s, kind, L, o, h);
+  };
+  // lifting of the prescribed displacement: g_{m,c} = (1 - mask_{m,c}) u0_c
+  std::vector<Tptr> lift;   // m * 2 + c (null: none)
+  for (int m = 0; m < q; ++m)
+    for (int c = 0; c < 2; ++c) {
+      Tptr acc = own(nullptr);
+      for (int t = 0; t < P->n_dir; ++t) {
+        if (P->dir_terms[3 * t] != c) continue;
+        auto gx = factor1d(P->dir_terms[3 * t + 1], P->patch_xy[2 * m]);
+        auto gy = factor1d(P->dir_terms[3 * t + 2], P->patch_xy[2 * m + 1]);
+        auto term = scaled(s, zkron(s, gx.get(), gy.get()).get(), P->dir_coef[t]);
+        acc = acc ? add(s, ar, acc.get(), 1.0, term.get(), 1.0, tin) : std::move(term);
+      }
+      if (acc) {
+        auto comp = add(s, ar, ones2.get(), 1.0, mask[2 * m + c].get(), -1.0, tin);
+        acc = hadamard(s, acc.get(), comp.get());
+        round_tt<double>(s, ar, acc.get(), tin, 0);
+      }
+      lift.push_back(std::move(acc));
+    }
+  std::vector<Tptr> Klift;   // sum over (p, b) of the unmasked block B_{ab,mp} times g_{p,b}
+  for (int i = 0; i < 2 * q; ++i) Klift.push_back(own(nullptr));
 
   // patch loads f^(m)_c
   std::vector<Tptr> load;   // m * 2 + c
@@ -524,6 +558,11 @@ void assemble(const qtt_problem* P, qtt_tensor** Kout, qtt_tensor** fout, cudaSt
           } else {
             continue;
           }
+          if (lift[2 * p + b]) {   // K g with the blocks before the masks
+            auto kg = prod(s, ar, B.get(), lift[2 * p + b].get(), tin);
+            Klift[2 * m + a] = Klift[2 * m + a] ? add(s, ar, Klift[2 * m + a].get(), 1.0, kg.get(), 1.0, tin)
+                                                : std::move(kg);
+          }
           // masks: diag(mask_{m,a}) B diag(mask_{p,b}) (+ diag(1 - mask) on the diagonal)
           auto Dl = diag_of(s, mask[2 * m + a].get());
           auto Dr = diag_of(s, mask[2 * p + b].get());
@@ -545,7 +584,9 @@ void assemble(const qtt_problem* P, qtt_tensor** Kout, qtt_tensor** fout, cudaSt
           auto pf = prod(s, ar, Pi[m * q + p].get(), load[2 * p + a].get(), 0);
           g = add(s, ar, g.get(), 1.0, pf.get(), 1.0, tin);
         }
+      if (Klift[2 * m + a]) g = add(s, ar, g.get(), 1.0, Klift[2 * m + a].get(), -1.0, tin);
       g = hadamard(s, g.get(), mask[2 * m + a].get());
+      if (lift[2 * m + a]) g = add(s, ar, g.get(), 1.0, lift[2 * m + a].get(), 1.0, tin);
       round_tt<double>(s, ar, g.get(), tin, 0);
       std::vector<int> ns, ms, is, js;
       if (q > 1) { ns.push_back(q); ms.push_back(1); is.push_back(m); js.push_back(0); }

@@ -8,6 +8,7 @@ import math
 import numpy as np
 import pytest
 import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 import workloads as W
 from oracle import fem
@@ -206,3 +207,38 @@ def test_load_total_force():
     f2 = fem.patch_load(prob2, 0)
     assert f2[1::2].sum() == pytest.approx(1.0, rel=1e-13)
     assert abs(f2[0::2]).max() == 0.0
+
+
+@pytest.mark.parametrize("patches", [((0, 0),), ((0, 0), (1, 0), (0, 1))])
+def test_patch_test_through_the_masked_duplicated_system(patches):
+    """Prescribed linear displacement on every outer side, no loads: the
+    masked concatenated system with the lifting f_bc = M (f - K g) + g
+    returns the linear field at every copy of every node (Q1 reproduces
+    linear fields exactly), one patch and the L-shape."""
+    import workloads as W
+    from oracle import indexing
+    prob = W.patch_test(3, patches)
+    K, f, free = fem.duplicated_system(prob)
+    u = spla.spsolve(sp.csc_matrix(K), f)
+    n, q = prob.n, prob.q
+    nn = n * n
+    h = 1.0 / (n - 1)
+    ii, jj = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    z = indexing.zorder(ii, jj, prob.L)
+    for m, (ox, oy) in enumerate(prob.patches):
+        x, y = ox + h * ii, oy + h * jj
+        ux = u[(z + nn * m).ravel()]
+        uy = u[(z + nn * m + nn * q).ravel()]
+        np.testing.assert_allclose(ux, (0.1 + 0.2 * x - 0.3 * y).ravel(), atol=1e-12)
+        np.testing.assert_allclose(uy, (-0.05 + 0.1 * x + 0.25 * y).ravel(), atol=1e-12)
+
+
+def test_prescribed_edge_duplicated_equals_merged():
+    """A nonzero prescribed edge: the masked duplicated system and Dirichlet
+    by elimination on the merged system give the same displacements."""
+    import workloads as W
+    prob = W.plate_prescribed_edge(4)
+    ud = fem.solve_duplicated(prob)
+    um, nm = fem.solve_merged(prob)
+    np.testing.assert_allclose(ud, fem.merged_to_qtt(prob, um, nm), rtol=0, atol=1e-12 * abs(ud).max())
+    assert abs(ud).max() > 1e-3

@@ -46,6 +46,9 @@ class Problem:
     body     : separable body-force terms (component, coeff, xkind, ykind).
     traction : constant edge tractions (patch, side, tx, ty).
     gamma    : concatenation penalty; 0 selects the mean diagonal of K_xx.
+    dirichlet: prescribed displacement u0 on the constrained sides, as
+               separable terms (component, coeff, xkind, ykind) of u0_c(x, y)
+               in global coordinates (empty: homogeneous conditions).
     """
 
     L: int
@@ -56,6 +59,7 @@ class Problem:
     body: List[Tuple[int, float, int, int]] = dataclasses.field(default_factory=list)
     traction: List[Tuple[int, int, float, float]] = dataclasses.field(default_factory=list)
     gamma: float = 0.0
+    dirichlet: List[Tuple[int, float, int, int]] = dataclasses.field(default_factory=list)
 
     @property
     def q(self) -> int:
@@ -112,6 +116,30 @@ def plate_top_traction(L: int, E: float, nu: float, amp: float, theta: float) ->
     return Problem(L=L, patches=[(0, 0)], E=E, nu=nu,
                    bc=[(CLAMP, 0, 0, 0)],
                    traction=[(0, TOP, amp * math.cos(theta), amp * math.sin(theta))])
+
+
+def patch_test(L: int, patches=((0, 0),), E: float = 5.0, nu: float = 0.3) -> Problem:
+    """Patch test: every outer side clamped to the linear field
+    u0 = (0.1 + 0.2 x - 0.3 y, -0.05 + 0.1 x + 0.25 y), no loads, so the
+    finite-element solution is u0 itself at every node."""
+    ps = list(patches)
+    occupied = set(ps)
+    bc = []
+    for (ox, oy) in ps:
+        nb = [(ox - 1, oy), (ox + 1, oy), (ox, oy - 1), (ox, oy + 1)]
+        bc.append(tuple(0 if q in occupied else CLAMP for q in nb))
+    u0 = [(0, 0.1, ONE, ONE), (0, 0.2, LIN, ONE), (0, -0.3, ONE, LIN),
+          (1, -0.05, ONE, ONE), (1, 0.1, LIN, ONE), (1, 0.25, ONE, LIN)]
+    return Problem(L=L, patches=ps, E=E, nu=nu, bc=bc, dirichlet=u0)
+
+
+def plate_prescribed_edge(L: int, E: float = 2.0, nu: float = 0.3) -> Problem:
+    """Plate clamped on the left with the right edge pulled to the
+    prescribed displacement u0 = (0.01 (1 + y), 0.02 sin(pi y)); top edge
+    traction (0, -0.5)."""
+    return Problem(L=L, patches=[(0, 0)], E=E, nu=nu, bc=[(CLAMP, CLAMP, 0, 0)],
+                   traction=[(0, TOP, 0.0, -0.5)],
+                   dirichlet=[(0, 0.01, ONE, ONE), (0, 0.01, ONE, LIN), (1, 0.02, ONE, SINPI)])
 
 
 def plate_params(seed: int, count: int) -> np.ndarray:
