@@ -305,6 +305,14 @@ int qtt_residual(const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* f,
 int qtt_residual_fe(const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* f,
                     double* out, void* stream);
 
+/* y = K x with the assembled operator applied as its finite-element stencil
+ * (the operator of qtt_residual_fe, masks and concatenation rows included)
+ * to a full vector.  x, y: DEVICE doubles in QTT_ORDER_CANONICAL (patch-major,
+ * DOF 2 (i + 2^L j) + c), n_elems = 2 q 4^L, no aliasing; caller-owned.  K
+ * must come from qtt_assemble_stiffness (QTT_EINVAL otherwise).  Takes
+ * device scratch; stream-ordered (does not synchronise). */
+int qtt_fe_apply(const qtt_tensor* K, const void* x, void* y, size_t n_elems, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Learned warm start (growth pattern of this engine; not in the paper)      */
 /* ------------------------------------------------------------------------ */

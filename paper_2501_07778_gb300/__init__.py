@@ -19,7 +19,7 @@ from ._lib import (QTT_F32, QTT_F64, QTT_MIXED, QTT_ORDER_CANONICAL, QTT_ORDER_Z
                    QttSolveOpts)
 
 __all__ = ["QTT", "QttError", "qtt_assemble_stiffness", "qtt_matvec", "qtt_round", "qtt_solve", "qtt_to_full",
-           "qtt_axpby", "qtt_norm", "qtt_residual", "qtt_residual_fe", "qtt_round_residual", "qtt_to_full_noalloc", "QTT_F64", "QTT_F32", "QTT_MIXED", "QTT_ORDER_Z_BLOCK",
+           "qtt_axpby", "qtt_norm", "qtt_residual", "qtt_residual_fe", "qtt_fe_apply", "qtt_round_residual", "qtt_to_full_noalloc", "QTT_F64", "QTT_F32", "QTT_MIXED", "QTT_ORDER_Z_BLOCK",
            "QTT_ORDER_CANONICAL", "lib"]
 
 
@@ -196,6 +196,17 @@ def qtt_residual_fe(K: QTT, u: QTT, f: QTT, stream=None) -> float:
     v = C.c_double()
     _check(lib().qtt_residual_fe(K.handle, u.handle, f.handle, C.byref(v), _stream(stream)), "qtt_residual_fe")
     return v.value
+
+
+def qtt_fe_apply(K: QTT, x, out=None, stream=None):
+    """K x for a full canonical FP64 CUDA tensor x (the assembled FE stencil)."""
+    import torch
+    assert x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()
+    if out is None:
+        out = torch.empty_like(x)
+    _check(lib().qtt_fe_apply(K.handle, C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()), x.numel(),
+                              _stream(stream)), "qtt_fe_apply")
+    return out
 
 
 def qtt_round_residual(K: QTT, u: QTT, f: QTT, rank: int, seed: int = 0, stream=None):

@@ -207,6 +207,42 @@ __global__ void fe_group_residual_kernel(double gamma, int ngroups, const int* g
   if ((threadIdx.x & 31) == 0 && r2 != 0.0) atomicAdd(&acc[0], r2);
 }
 
+// y = K_bc x at nodes held by one copy (y holds the stencil output)
+__global__ void fe_rows_kernel(long long total, const double* __restrict__ x, const unsigned char* __restrict__ flags,
+                               double* __restrict__ y) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const unsigned char fl = flags[t];
+    if (fl & FE_SHARED) continue;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+      if (fl & (1 << c)) y[2 * t + c] = x[2 * t + c];
+  }
+}
+
+// y = K_bc x at shared nodes: summed stiffness rows plus gamma coupling
+// (one thread per group; reads the stencil rows ys, writes y)
+__global__ void fe_group_rows_kernel(double gamma, int ngroups, const int* gstart, const long long* gidx,
+                                     const double* __restrict__ x, const unsigned char* __restrict__ flags,
+                                     const double* __restrict__ ys, double* __restrict__ y) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= ngroups) return;
+  const int k0 = gstart[g], k1 = gstart[g + 1];
+  const double cnt = (double)(k1 - k0);
+  const unsigned char fl = flags[gidx[k0]];
+  for (int c = 0; c < 2; ++c) {
+    const bool fixed = (fl & (1 << c)) != 0;
+    double sy = 0.0, su = 0.0;
+    for (int k = k0; k < k1; ++k) {
+      sy += ys[2 * gidx[k] + c];
+      su += fixed ? 0.0 : x[2 * gidx[k] + c];
+    }
+    for (int k = k0; k < k1; ++k) {
+      const long long v = gidx[k];
+      y[2 * v + c] = fixed ? x[2 * v + c] : sy + gamma * (cnt * x[2 * v + c] - su);
+    }
+  }
+}
+
 // Copies of physical nodes shared by two or more patches, as index lists
 // into the canonical node array (m n^2 + i + n j).  Patches are unit squares
 // at integer offsets, so only patch-boundary nodes can coincide.
@@ -237,6 +273,49 @@ void shared_groups(const FeOperator& op, std::vector<int>& start, std::vector<lo
 }  // namespace
 
 bool has_fe_operator(const qtt_tensor* K) { return K && K->fe && K->prec == QTT_F64; }
+
+// y = K_bc x for full canonical vectors x, y (device, 2 q n^2 doubles each)
+void fe_apply(cudaStream_t s, const qtt_tensor* K, const double* x, double* y) {
+  QTT_REQUIRE(has_fe_operator(K), "fe_apply: K does not come from qtt_assemble_stiffness");
+  const FeOperator& op = *K->fe;
+  const int n = 1 << op.L;
+  const long long nn = (long long)n * n, total = nn * op.q;
+  FeParams p{};
+  p.L = op.L;
+  p.q = op.q;
+  p.n = n;
+  p.gamma = op.gamma;
+  element_matrix(op.E, op.nu, 1.0 / (n - 1.0), p.Ke);
+  for (int i = 0; i < 4 * op.q; ++i) p.bc[i] = op.bc[i];
+  Arena ar(s);
+  unsigned char* flags = ar.alloc<unsigned char>(total);
+  fe_flags_kernel<<<grid_for_n(total, 8), 256, 0, s>>>(p, flags);
+  QTT_CHECK_LAUNCH();
+  std::vector<int> gstart;
+  std::vector<long long> gidx;
+  shared_groups(op, gstart, gidx);
+  const int ngroups = (int)gstart.size() - 1;
+  int* d_start = nullptr;
+  long long* d_idx = nullptr;
+  if (ngroups > 0) {
+    d_start = ar.alloc<int>(gstart.size());
+    d_idx = ar.alloc<long long>(gidx.size());
+    QTT_CUDA(cudaMemcpyAsync(d_start, gstart.data(), sizeof(int) * gstart.size(), cudaMemcpyHostToDevice, s));
+    QTT_CUDA(cudaMemcpyAsync(d_idx, gidx.data(), sizeof(long long) * gidx.size(), cudaMemcpyHostToDevice, s));
+    fe_group_flags_kernel<<<(ngroups + 127) / 128, 128, 0, s>>>(ngroups, d_start, d_idx, flags);
+    QTT_CHECK_LAUNCH();
+  }
+  double* ys = ngroups > 0 ? ar.alloc<double>(2 * total) : y;   // stencil rows
+  fe_stencil_kernel<<<grid_for_n(total, 8), 256, 0, s>>>(p, x, flags, ys);
+  QTT_CHECK_LAUNCH();
+  if (ngroups > 0) {
+    QTT_CUDA(cudaMemcpyAsync(y, ys, sizeof(double) * 2 * total, cudaMemcpyDeviceToDevice, s));
+    fe_group_rows_kernel<<<(ngroups + 127) / 128, 128, 0, s>>>(op.gamma, ngroups, d_start, d_idx, x, flags, ys, y);
+    QTT_CHECK_LAUNCH();
+  }
+  fe_rows_kernel<<<grid_for_n(total, 8), 256, 0, s>>>(total, x, flags, y);
+  QTT_CHECK_LAUNCH();
+}
 
 // ||f - K (u + u2)|| / ||f|| (u2 may be NULL) with K applied as the
 // assembled finite-element operator
@@ -301,6 +380,26 @@ double residual_fe(cudaStream_t s, const qtt_tensor* K, const qtt_tensor* u, con
 }
 
 }  // namespace qtt
+
+extern "C" int qtt_fe_apply(const qtt_tensor* K, const void* x, void* y, size_t n_elems, void* stream) {
+  try {
+    QTT_REQUIRE(K && x && y, "qtt_fe_apply: null argument");
+    QTT_REQUIRE(qtt::has_fe_operator(K), "qtt_fe_apply: K does not come from qtt_assemble_stiffness");
+    const long long nn = 1LL << (2 * K->fe->L);
+    QTT_REQUIRE((long long)n_elems == 2 * K->fe->q * nn, "qtt_fe_apply: n_elems must be 2 q 4^L");
+    QTT_REQUIRE(x != y, "qtt_fe_apply: x and y must not alias");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    qtt::StreamScope scope_(s);
+    qtt::fe_apply(s, K, static_cast<const double*>(x), static_cast<double*>(y));
+    return QTT_OK;
+  } catch (const qtt::QttError& e) {
+    qtt::set_last_error(e.what());
+    return e.code;
+  } catch (const std::exception& e) {
+    qtt::set_last_error(e.what());
+    return QTT_EINVAL;
+  }
+}
 
 extern "C" int qtt_residual_fe(const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* f, double* out,
                                void* stream) {
