@@ -558,6 +558,7 @@ def main(argv=None):
                             "checks": [i["checks"] for i in infos],
                             "check_ms": [round(i["check_ms"], 1) for i in infos],
                             "refine_ms": [round(i["refine_ms"], 1) for i in infos]},
+            "autotune": q.autotune_table(),
             "plain": plain, "warm_start": ws_info, "gpu_launches": int(launches), "clocks": clocks,
             "roofline": roofline, "peaks": {k: peaks.get(k) for k in ("fp64_tflops", "fp32_tflops", "hbm_gbs",
                                                                        "bf16_tflops")},

@@ -228,10 +228,12 @@ typedef struct {
   double inner_tol;       /* relative tolerance of each refinement's correction
                              solve (<= 0: 1e-3) */
   int verbose;            /* print per-sweep progress to stderr */
-  int tensor_cores;       /* QTT_MIXED: >= 0 runs the FP32 local operator of the
-                             Krylov iterations at ranks >= 32 as tcgen05 3xTF32
-                             GEMMs (sm_103); < 0 keeps it on the FP32 SIMT
-                             pipes */
+  int tensor_cores;       /* QTT_MIXED, FP32 local operator at ranks >= 32:
+                             0 = the autotuner chooses per rank bucket between
+                             tcgen05 3xTF32 GEMMs (sm_103) and the persistent
+                             SIMT CG kernel by their measured time per
+                             iteration; > 0 = always tensor cores; < 0 = always
+                             SIMT */
 } qtt_solve_opts;
 
 typedef struct {
@@ -378,6 +380,14 @@ int qtt_gemm_tf32x3(int M, int N, int K, const float* A, int lda, const float* B
 /* ------------------------------------------------------------------------ */
 /* Diagnostics (not part of the method)                                      */
 /* ------------------------------------------------------------------------ */
+
+/* The autotuner's table for the current device: for every rank bucket of
+ * the FP32 local operator met so far (b = floor(2 log2 r) for the left and
+ * right ranks), the measured microseconds per Krylov iteration on the
+ * tensor cores (us_tc) and in the persistent SIMT kernel (us_simt), -1 while
+ * not yet timed; later local solves in a bucket take the faster path.  Fills
+ * up to cap entries of each (non-NULL) array; *count = entries in the table. */
+int qtt_autotune_table(int cap, int* count, int* r0_bucket, int* r1_bucket, double* us_tc, double* us_simt);
 
 /* Number of CUDA kernels this library has launched in this process. */
 unsigned long long qtt_kernel_launches(void);

@@ -218,6 +218,20 @@ def qtt_round_residual(K: QTT, u: QTT, f: QTT, rank: int, seed: int = 0, stream=
     return QTT(h), kept.value
 
 
+def autotune_table():
+    """The autotuner's decisions on this device: list of dicts (rank buckets,
+    microseconds per Krylov iteration on tensor cores and SIMT)."""
+    n = C.c_int()
+    lib().qtt_autotune_table(0, C.byref(n), None, None, None, None)
+    k = n.value
+    b0, b1 = (C.c_int * max(1, k))(), (C.c_int * max(1, k))()
+    tc, sm = (C.c_double * max(1, k))(), (C.c_double * max(1, k))()
+    lib().qtt_autotune_table(k, C.byref(n), b0, b1, tc, sm)
+    return [{"r0_bucket": b0[i], "r1_bucket": b1[i], "us_tc": tc[i], "us_simt": sm[i],
+             "choice": ("tc" if 0 <= tc[i] < sm[i] else "simt") if tc[i] >= 0 and sm[i] >= 0 else "timing"}
+            for i in range(k)]
+
+
 def make_problem_struct(prob, tol: float = 0.0):
     """Marshal a workloads.Problem into the C struct (arrays kept alive on the
     returned struct)."""

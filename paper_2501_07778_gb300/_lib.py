@@ -79,6 +79,7 @@ SIGNATURES = {
     "qtt_ws_adam": (C.c_int, [C.c_int, P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int, P]),
     "qtt_ws_to_tensor": (C.c_int, [P, C.c_int, IP, C.c_int, C.c_double, PP, P]),
     "qtt_gemm_tf32x3": (C.c_int, [C.c_int, C.c_int, C.c_int, P, C.c_int, P, C.c_int, P, C.c_int, P]),
+    "qtt_autotune_table": (C.c_int, [C.c_int, IP, IP, IP, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "qtt_kernel_launches": (C.c_ulonglong, []),
     "qtt_device_allocations": (C.c_ulonglong, []),
     "qtt_measure_fma_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double), P]),

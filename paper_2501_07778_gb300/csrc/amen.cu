@@ -23,6 +23,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <vector>
 
 #include <cooperative_groups.h>
@@ -410,6 +411,51 @@ void apply_local(cudaStream_t s, Arena& sc, const U* PhiL, int ra, int rc, const
 // ---------------------------------------------------------------------------
 inline int pad4(int x) { return (x + 3) / 4 * 4; }
 
+// ---------------------------------------------------------------------------
+// Autotuner of the FP32 local operator.  Per GPU and per rank bucket of the
+// local system (r0, r1 rounded down to half-octaves), the first local solve
+// runs its Krylov iterations on the tensor cores (TcLocalOp), the next one
+// in the persistent SIMT CG kernel; CUDA events give each one's time per
+// iteration, and every later solve in the bucket takes the faster path.
+// ---------------------------------------------------------------------------
+struct TuneEntry {
+  int dev, b0, b1;
+  double us_tc = -1.0, us_simt = -1.0;
+};
+std::mutex g_tune_mu;
+std::vector<TuneEntry> g_tune;
+
+inline int half_octave(int r) { return (int)std::floor(2.0 * std::log2((double)std::max(1, r))); }
+
+// 1: tensor cores, 0: SIMT, 2: time the tensor cores now, 3: time SIMT now
+int tune_choice(int r0, int r1) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int b0 = half_octave(r0), b1 = half_octave(r1);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (auto& e : g_tune)
+    if (e.dev == dev && e.b0 == b0 && e.b1 == b1) {
+      if (e.us_tc < 0) return 2;
+      if (e.us_simt < 0) return 3;
+      return e.us_tc < e.us_simt ? 1 : 0;
+    }
+  g_tune.push_back(TuneEntry{dev, b0, b1});
+  return 2;
+}
+
+void tune_record(int r0, int r1, bool tc, double us) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int b0 = half_octave(r0), b1 = half_octave(r1);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (auto& e : g_tune)
+    if (e.dev == dev && e.b0 == b0 && e.b1 == b1) {
+      if (tc && e.us_tc < 0) e.us_tc = us;
+      if (!tc && e.us_simt < 0) e.us_simt = us;
+      return;
+    }
+}
+
 inline TcIdxMap idx1(int n0, long long s0) {
   TcIdxMap m{};
   m.cnt = 1;
@@ -506,6 +552,7 @@ struct Amen {
   int max_rank, kick, max_sweeps, ndir, restart, cycles, verbose;
   bool mixed_local = false;   // FP32 operator inside the local GMRES cycles
   bool tensor_cores = false;  // the FP32 local operator on tcgen05 (3xTF32) at ranks >= 32
+  bool tc_always = false;     // ... in every bucket, not only where the autotuner found it faster
   int* tc_err = nullptr;      // device word set by a tensor-core kernel whose bounded wait gave up
   double global_check = 0.0;  // > 0: check the FP64 global residual once max local <= global_check * tol
   bool stall_exit = false;    // stop when two sweeps in a row fail to halve the best max local residual
@@ -782,8 +829,18 @@ struct Amen {
       inv_diag_kernel<T, U><<<(N + 255) / 256, 256, 0, s>>>(dg, minv, N);
       QTT_CHECK_LAUNCH();
     }
-    const bool use_tc = sizeof(U) == 4 && sizeof(T) == 8 && tensor_cores && op32.PL && tc_err && r0 >= 32 &&
-                        r1 >= 32 && tc_available();
+    const bool tc_ok = sizeof(U) == 4 && sizeof(T) == 8 && tensor_cores && op32.PL && tc_err && r0 >= 32 &&
+                       r1 >= 32 && tc_available() && persistent_cg_grid() > 0;
+    const int choice = tc_ok ? (tc_always ? 1 : tune_choice(r0, r1)) : 0;
+    const bool use_tc = tc_ok && (choice == 1 || choice == 2);
+    const bool timing = tc_ok && (choice == 2 || choice == 3);
+    cudaEvent_t tev0 = nullptr, tev1 = nullptr;
+    double tune_ms = 0.0;
+    long long tune_iters = 0;
+    if (timing) {
+      QTT_CUDA(cudaEventCreate(&tev0));
+      QTT_CUDA(cudaEventCreate(&tev1));
+    }
     TcLocalOp tl;
     if (use_tc)
       tl.build(s, sc, reinterpret_cast<const float*>(PL), reinterpret_cast<const float*>(Ak),
@@ -806,6 +863,7 @@ struct Amen {
       double* rr_new = sc4 + 1;
       double* pq = sc4 + 2;
       dotp<U>(s, r, p, N, rr_old);
+      if (timing) QTT_CUDA(cudaEventRecord(tev0, s));
       if (use_tc) {
         // every iteration on the tensor cores: B p by three 3xTF32 GEMMs,
         // the CG scalars on the device
@@ -881,6 +939,14 @@ struct Amen {
           std::swap(rr_old, rr_new);
         }
       }
+      if (timing) {
+        QTT_CUDA(cudaEventRecord(tev1, s));
+        QTT_CUDA(cudaEventSynchronize(tev1));
+        float ms = 0.f;
+        QTT_CUDA(cudaEventElapsedTime(&ms, tev0, tev1));
+        tune_ms += ms;
+        tune_iters += m;
+      }
       if (sizeof(U) != sizeof(T)) {
         convert<U, T>(s, d, wT, N);
         axpby<T>(s, N, T(1), wT, T(1), xk);
@@ -888,6 +954,11 @@ struct Amen {
         axpby<T>(s, N, T(1), reinterpret_cast<const T*>(d), T(1), xk);
       }
       if (info) info->local_iters += m;
+    }
+    if (timing) {
+      if (tune_iters > 0) tune_record(r0, r1, use_tc, 1e3 * tune_ms / (double)tune_iters);
+      cudaEventDestroy(tev0);
+      cudaEventDestroy(tev1);
     }
     return rel;
   }
@@ -1216,6 +1287,7 @@ int amen_run(cudaStream_t s, const qtt_tensor* K, const qtt_tensor* f, qtt_tenso
   am.info = info;
   am.mixed_local = mixed_local;
   am.tensor_cores = mixed_local && o.tensor_cores >= 0;
+  am.tc_always = o.tensor_cores > 0;
   if (am.tensor_cores) {
     am.tc_err = ar.alloc<int>(1);
     QTT_CUDA(cudaMemsetAsync(am.tc_err, 0, sizeof(int), s));
@@ -1385,6 +1457,26 @@ int solve(const qtt_tensor* K, const qtt_tensor* f, const qtt_tensor* x0, const 
 }
 
 }  // namespace qtt
+
+extern "C" int qtt_autotune_table(int cap, int* count, int* r0_bucket, int* r1_bucket, double* us_tc,
+                                  double* us_simt) {
+  std::lock_guard<std::mutex> lk(qtt::g_tune_mu);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int n = 0;
+  for (const auto& e : qtt::g_tune) {
+    if (e.dev != dev) continue;
+    if (n < cap) {
+      if (r0_bucket) r0_bucket[n] = e.b0;
+      if (r1_bucket) r1_bucket[n] = e.b1;
+      if (us_tc) us_tc[n] = e.us_tc;
+      if (us_simt) us_simt[n] = e.us_simt;
+    }
+    ++n;
+  }
+  if (count) *count = n;
+  return QTT_OK;
+}
 
 extern "C" int qtt_solve(const qtt_tensor* K, const qtt_tensor* f, const qtt_tensor* x0, const qtt_tensor* z0,
                          const qtt_solve_opts* opts, qtt_tensor** x, qtt_solve_info* info, void* stream) {

@@ -42,11 +42,11 @@ def _merged_in_qtt_order(prob):
     return fem.merged_to_qtt(prob, u, node_map)
 
 
-@pytest.mark.parametrize("tensor_cores", [0, -1])
+@pytest.mark.parametrize("tensor_cores", [1, -1])
 def test_mixed_solve_with_tensor_core_local_operator(tensor_cores):
     """QTT_MIXED with the CG forced on every core (local_direct_max = 1): with
-    tensor_cores >= 0 the FP32 local operator at ranks >= 32 runs as tcgen05
-    3xTF32 GEMMs (profile class 10 launches), otherwise on the SIMT pipes;
+    tensor_cores > 0 the FP32 local operator at ranks >= 32 runs as tcgen05
+    3xTF32 GEMMs (profile class 10 launches), with < 0 on the SIMT pipes;
     both reach the sparse direct solution."""
     import workloads as W
     lib = q.lib()
@@ -63,7 +63,7 @@ def test_mixed_solve_with_tensor_core_local_operator(tensor_cores):
         lib.qtt_profile_enable(0)
     lib.qtt_profile_read(10, C.byref(ms), C.byref(fl), C.byref(by), C.byref(n))
     lib.qtt_profile_read(-1, None, None, None, None)
-    if tensor_cores >= 0:
+    if tensor_cores > 0:
         assert n.value > 0, "the tensor-core GEMM did not run"
     else:
         assert n.value == 0
@@ -72,3 +72,22 @@ def test_mixed_solve_with_tensor_core_local_operator(tensor_cores):
     err = np.linalg.norm(ug - ref) / np.linalg.norm(ref)
     assert info["rc"] == 0 and info["rel_residual"] <= 1e-9, info
     assert err <= 1e-7, (err, info)
+
+
+def test_autotuner_times_both_paths_and_solves():
+    """tensor_cores = 0: the autotuner times the tensor-core and the SIMT
+    operator in every rank bucket it meets and the solve stays exact."""
+    import workloads as W
+    prob = W.plate_top_traction(8, 40.0, 0.33, 1.3, 2.0)
+    K, f = q.qtt_assemble_stiffness(prob)
+    for _ in range(2):      # the second solve meets the buckets the first one timed
+        u, info = q.qtt_solve(K, f, tol=1e-9, precision=q.QTT_MIXED, local_direct_max=1, kick_rank=8,
+                              max_sweeps=30, tensor_cores=0)
+        assert info["rc"] == 0 and info["rel_residual"] <= 1e-9, info
+    table = q.autotune_table()
+    assert table, "no rank bucket reached the autotuner"
+    timed = [e for e in table if e["us_tc"] > 0 and e["us_simt"] > 0]
+    assert timed, table
+    ref = _merged_in_qtt_order(prob)
+    ug = q.qtt_to_full(u).cpu().numpy()
+    assert np.linalg.norm(ug - ref) / np.linalg.norm(ref) <= 1e-7
