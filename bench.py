@@ -51,6 +51,8 @@ METRIC = "QTT solves/sec at rel. residual 1e-8 (L=12); fast form vs plain FP64 G
 ACCEPT = 1e-8
 MAX_SWEEPS = 24
 KICK_RANK = 8
+TENSOR_CORES = 0
+LOCAL_DIRECT_MAX = 0
 _T0 = time.perf_counter()
 CLASSES = {0: "gemm_f64", 1: "gemm_f32", 2: "core_product", 3: "qr_panel", 4: "jacobi_svd", 5: "lu_panel",
            6: "permute", 7: "to_full", 8: "pcg_f32", 9: "jacobi_f32", 10: "tc_gemm_tf32x3"}
@@ -74,6 +76,10 @@ def parse(argv=None):
     ap.add_argument("--workers", type=int, default=1, help="concurrent solves when --batch > 1")
     ap.add_argument("--max-sweeps", type=int, default=24)
     ap.add_argument("--kick-rank", type=int, default=8, help="residual-proxy rank of the AMEn enrichment")
+    ap.add_argument("--local-direct-max", type=int, default=0,
+                    help="local systems up to this size use dense LU (0: the library default)")
+    ap.add_argument("--tensor-cores", type=int, default=0,
+                    help="FP32 local operator: 0 autotuned tcgen05/SIMT, 1 always tensor cores, -1 always SIMT")
     ap.add_argument("--L", type=int, default=12)
     ap.add_argument("--tol", type=float, default=ACCEPT)
     ap.add_argument("--plain-solves", type=int, default=1,
@@ -180,7 +186,8 @@ def combine_ranks(ms: float, accepted: int, total: int, dist=None, device: str =
 def solve_kw(form: str, tol: float):
     import paper_2501_07778_gb300 as q
     prec = q.QTT_F64 if form == "plain" else q.QTT_MIXED
-    return dict(tol=tol, precision=prec, kick_rank=KICK_RANK, max_sweeps=MAX_SWEEPS)
+    return dict(tol=tol, precision=prec, kick_rank=KICK_RANK, max_sweeps=MAX_SWEEPS, tensor_cores=TENSOR_CORES,
+                local_direct_max=LOCAL_DIRECT_MAX)
 
 
 def problem_bytes(prob) -> int:
@@ -415,9 +422,11 @@ def main(argv=None):
             dist.barrier()
         torch.cuda.synchronize()
 
-    global MAX_SWEEPS, KICK_RANK
+    global MAX_SWEEPS, KICK_RANK, TENSOR_CORES, LOCAL_DIRECT_MAX
     MAX_SWEEPS = args.max_sweeps
     KICK_RANK = args.kick_rank
+    TENSOR_CORES = args.tensor_cores
+    LOCAL_DIRECT_MAX = args.local_direct_max
     batch = max(1, args.batch)
     nsteps = args.warmup + args.steps
     P, probs = workload(args.L, nsteps * batch, rank, world)
@@ -549,6 +558,7 @@ def main(argv=None):
                        "batch_per_rank": batch, "workers": args.workers if batch > 1 else 1,
                        "learned_warm_start": ws_info is not None and bool(ws_info.get("used")),
                        "accept_rel_residual": args.tol, "kick_rank": args.kick_rank, "max_sweeps": args.max_sweeps,
+                       "tensor_cores": {0: "autotuned", 1: "always"}.get(args.tensor_cores, "off"),
                        "l2": "flushed (256 MB write) before every timed step"},
             "accepted": int(acc_all), "solved": int(tot_all),
             "solve_stats": {"sweeps": [i["sweeps"] for i in infos], "max_rank": [i["max_rank"] for i in infos],

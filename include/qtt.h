@@ -224,7 +224,7 @@ typedef struct {
   int local_max_cycles;   /* GMRES restart cycles per local solve (<= 0: 8) */
   int precision;          /* QTT_F64, QTT_F32 or QTT_MIXED */
   int refine_max;         /* QTT_F64 / QTT_MIXED: maximum outer refinement steps
-                             (0: 4; < 0: none, the sweeps alone decide) */
+                             (0: 6; < 0: none, the sweeps alone decide) */
   double inner_tol;       /* relative tolerance of each refinement's correction
                              solve (<= 0: 1e-3) */
   int verbose;            /* print per-sweep progress to stderr */

@@ -1391,7 +1391,7 @@ int solve(const qtt_tensor* K, const qtt_tensor* f, const qtt_tensor* x0, const 
     // the level of FP64 noise only).
     const bool mixed = o.precision == QTT_MIXED;
     const double inner = o.inner_tol > 0 ? o.inner_tol : 1e-3;
-    const int refine_max = o.refine_max > 0 ? o.refine_max : (o.refine_max < 0 ? 0 : 4);
+    const int refine_max = o.refine_max > 0 ? o.refine_max : (o.refine_max < 0 ? 0 : 6);
     Tptr u = x0 ? own(tensor_clone(x0, QTT_F64, s)) : default_x0(s, f, QTT_F64);
     Tptr z = z0 ? own(tensor_clone(z0, QTT_F64, s)) : default_z0(s, f, rho, QTT_F64);
     rc = amen_run<double>(s, K, f, u.get(), z.get(), o.tol, o, inf, mixed, refine_max > 0);

@@ -568,7 +568,17 @@ void svd(cudaStream_t s, Arena& ar, int m, int n, T* A, int lda, T* U, int ldu, 
   T* Vm = ar.alloc<T>((size_t)n * n);
   set_identity_kernel<T><<<grid_for((long long)n * n), 256, 0, s>>>(Vm, n, n, n);
   QTT_CHECK_LAUNCH();
-  if (sizeof(T) == 8 && n >= 24) {
+  static int coop_dev = -1;
+  if (coop_dev < 0) {
+    int dev = 0, v = 0;
+    coop_dev = (cudaGetDevice(&dev) == cudaSuccess &&
+                cudaDeviceGetAttribute(&v, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && v) ? 1 : 0;
+    cudaGetLastError();
+  }
+  // With cooperative launch the FP64 sweeps run on many SMs from the start
+  // (a round costs one grid barrier plus one pair per warp); the FP32
+  // pre-sweeps below pay off only when the FP64 sweeps would share one SM.
+  if (sizeof(T) == 8 && n >= 24 && !coop_dev) {
     // Mixed-precision preconditioning (one CTA runs the Jacobi sweeps, and
     // one SM has 1/64 of its FP32 rate in FP64): the sweeps run first in
     // FP32 on an FP32 copy of R, their rotations V32 are made orthogonal to

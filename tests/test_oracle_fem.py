@@ -242,3 +242,24 @@ def test_prescribed_edge_duplicated_equals_merged():
     um, nm = fem.solve_merged(prob)
     np.testing.assert_allclose(ud, fem.merged_to_qtt(prob, um, nm), rtol=0, atol=1e-12 * abs(ud).max())
     assert abs(ud).max() > 1e-3
+
+
+def test_manufactured_plate_load_is_the_exact_body_force():
+    """The body force of workloads.plate_manufactured is -div sigma of
+    u = (sin pi x sin pi y, 0): the sparse FE solution converges to u at
+    O(h^2) in the nodal max norm."""
+    import workloads as W
+    errs = []
+    for L in (4, 5, 6):
+        prob = W.plate_manufactured(L, E=3.0, nu=0.25)
+        um, nm = fem.solve_merged(prob)
+        n = prob.n
+        h = 1.0 / (n - 1)
+        g = nm[0]
+        x = h * np.arange(n)
+        ux = um[2 * g]                                   # [i, j]
+        exact = np.outer(np.sin(np.pi * x), np.sin(np.pi * x))
+        errs.append(np.abs(ux - exact).max())
+        assert np.abs(um[2 * g + 1]).max() <= 5 * errs[-1] + 1e-12
+    rates = [np.log2(a / b) / np.log2((2 ** (L + 1) - 1) / (2 ** L - 1)) for a, b, L in zip(errs, errs[1:], (4, 5))]
+    assert all(1.8 <= r <= 2.3 for r in rates), (errs, rates)

@@ -142,6 +142,18 @@ def plate_prescribed_edge(L: int, E: float = 2.0, nu: float = 0.3) -> Problem:
                    dirichlet=[(0, 0.01, ONE, ONE), (0, 0.01, ONE, LIN), (1, 0.02, ONE, SINPI)])
 
 
+def plate_manufactured(L: int, E: float = 1.0, nu: float = 0.3) -> Problem:
+    """Fully clamped plate whose exact plane-stress solution is
+    u = (sin(pi x) sin(pi y), 0): the body force -div sigma(u) is
+    f_x = e pi^2 (3 - nu) / 2 sin(pi x) sin(pi y),
+    f_y = -e pi^2 (1 + nu) / 2 cos(pi x) cos(pi y), e = E / (1 - nu^2).
+    A smooth solution without corner singularities (the Q1 orders hold)."""
+    e = E / (1.0 - nu * nu)
+    return Problem(L=L, patches=[(0, 0)], E=E, nu=nu, bc=[(CLAMP, CLAMP, CLAMP, CLAMP)],
+                   body=[(0, e * math.pi ** 2 * (3.0 - nu) / 2.0, SINPI, SINPI),
+                         (1, -e * math.pi ** 2 * (1.0 + nu) / 2.0, COSPI, COSPI)])
+
+
 def plate_params(seed: int, count: int) -> np.ndarray:
     """(E, nu, amp, theta) rows: E log-uniform in [1, 1000], nu ~ U(0.2, 0.45),
     amp ~ U(0.5, 2), theta ~ U(0, 2 pi)."""
