@@ -29,14 +29,35 @@ extern "C" int qtt_solve_batched(int count, const qtt_tensor* const* K, const qt
     QTT_CUDA(cudaGetDevice(&dev));
     const int W = std::max(1, std::min(nworkers > 0 ? nworkers : 8, count));
     cudaStream_t caller = reinterpret_cast<cudaStream_t>(stream);
+    // Streams and events are released on every path, and the caller's
+    // stream waits for every worker stream that was created, also when an
+    // error ends the call early.
+    struct Streams {
+      cudaStream_t caller;
+      cudaEvent_t ready = nullptr;
+      std::vector<cudaStream_t> s;
+      ~Streams() {
+        for (cudaStream_t w : s) {
+          cudaEvent_t done;
+          if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) == cudaSuccess) {
+            if (cudaEventRecord(done, w) == cudaSuccess) cudaStreamWaitEvent(caller, done, 0);
+            cudaEventDestroy(done);
+          }
+          cudaStreamDestroy(w);
+        }
+        if (ready) cudaEventDestroy(ready);
+        cudaGetLastError();
+      }
+    } st{caller};
     // inputs may still be in flight on the caller's stream
-    cudaEvent_t ready;
-    QTT_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
-    QTT_CUDA(cudaEventRecord(ready, caller));
-    std::vector<cudaStream_t> streams(W);
+    QTT_CUDA(cudaEventCreateWithFlags(&st.ready, cudaEventDisableTiming));
+    QTT_CUDA(cudaEventRecord(st.ready, caller));
+    std::vector<cudaStream_t>& streams = st.s;
     for (int w = 0; w < W; ++w) {
-      QTT_CUDA(cudaStreamCreateWithFlags(&streams[w], cudaStreamNonBlocking));
-      QTT_CUDA(cudaStreamWaitEvent(streams[w], ready, 0));
+      cudaStream_t ws;
+      QTT_CUDA(cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking));
+      streams.push_back(ws);
+      QTT_CUDA(cudaStreamWaitEvent(ws, st.ready, 0));
     }
     std::atomic<int> next{0};
     std::atomic<int> first_error{QTT_OK};
@@ -75,16 +96,8 @@ extern "C" int qtt_solve_batched(int count, const qtt_tensor* const* K, const qt
     std::vector<std::thread> threads;
     for (int w = 0; w < W; ++w) threads.emplace_back(worker, w);
     for (auto& t : threads) t.join();
-    for (int w = 0; w < W; ++w) {
-      cudaEvent_t done;
-      QTT_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
-      QTT_CUDA(cudaEventRecord(done, streams[w]));
-      QTT_CUDA(cudaStreamWaitEvent(caller, done, 0));
-      cudaEventDestroy(done);
-      cudaStreamDestroy(streams[w]);
-    }
-    cudaEventDestroy(ready);
-    // results now belong to the caller's stream (the worker streams are gone)
+    // results belong to the caller's stream (the worker streams end with
+    // this call, after the caller's stream has been made to wait on them)
     for (int i = 0; i < count; ++i)
       if (x[i]) x[i]->stream = caller;
     if (first_error.load() != QTT_OK) {

@@ -7,11 +7,14 @@ every record holds what the paper plots against d:
     sum_k r_{k-1} n_k r_k and effective rank (Section 4);
   * the memory of the assembled K and f and of the solution (FP64 cores);
   * the solve's time, sweeps and FP64 relative residual;
-  * the error against a self-refined reference: the solution at the finest
-    level ref_level, interpolated (bilinear on each patch, i.e. the Q1
-    field itself) to every coarser mesh, in the relative discrete L2 norm
-    and in the energy seminorm sqrt(e^T K e) through the assembled operator
-    (qtt_fe_apply).
+  * the error against a self-refined reference, the solution at the finest
+    level ref_level: the coarse Q1 field prolonged (bilinear on each patch)
+    to the reference mesh, e = u_ref - P u_h, in the relative L2 norm and
+    the energy seminorm sqrt(e^T K e / u_ref^T K u_ref) of the reference
+    mesh (err_l2, err_energy: the errors of the field, O(h^2) and O(h) for
+    smooth solutions); and the nodal difference u_h - I u_ref on the coarse
+    mesh (err_l2_nodal, err_energy_nodal: superconvergent, O(h^2) in both on
+    these uniform meshes).  Operators are applied by qtt_fe_apply.
 `rates` fits the algebraic order of the errors in h and the exponential
 rate of the error in N_d.  Every number comes from the library's kernels;
 the interpolation and the norms are elementwise device tensor operations.
@@ -37,12 +40,13 @@ def _grid(u_can, q: int, n: int):
     return u_can.view(q, n, n, 2).permute(0, 3, 1, 2)
 
 
-def interpolate(u_fine, q: int, L_fine: int, L_coarse: int):
-    """The Q1 field of a fine canonical vector evaluated at the nodes of a
-    coarser mesh of the same patches (bilinear on every patch); returns a
-    canonical vector of the coarse mesh."""
+def interpolate(u_src, q: int, L_src: int, L_dst: int):
+    """The Q1 field of a canonical vector on the level-L_src mesh evaluated
+    at the nodes of the level-L_dst mesh of the same patches (bilinear on
+    every patch); returns a canonical vector of the destination mesh."""
     import torch
-    nf, nc = 1 << L_fine, 1 << L_coarse
+    u_fine = u_src
+    nf, nc = 1 << L_src, 1 << L_dst
     U = _grid(u_fine, q, nf)                                   # [m, c, j, i]
     t = torch.arange(nc, dtype=torch.float64, device=u_fine.device) * ((nf - 1) / (nc - 1))
     i0 = torch.clamp(t.floor().long(), max=nf - 2)
@@ -80,18 +84,21 @@ def study(make: Callable[[int], object], levels: List[int], ref_level: int, tol:
           precision: int = QTT_MIXED, **solve_kw) -> List[Dict]:
     """Records for every level, with errors against the ref_level solution."""
     import torch
-    ref_rec, u_ref, _ = level_record(make, ref_level, tol=tol, precision=precision, **solve_kw)
+
+    def rel(e, ref, K):
+        l2 = float(torch.linalg.norm(e) / torch.linalg.norm(ref))
+        en = float(torch.sqrt(torch.clamp(torch.dot(e, qtt_fe_apply(K, e)), min=0.0)) /
+                   torch.sqrt(torch.dot(ref, qtt_fe_apply(K, ref))))
+        return l2, en
+
+    ref_rec, u_ref, K_ref = level_record(make, ref_level, tol=tol, precision=precision, **solve_kw)
     q = make(ref_level).q
     out = []
     for L in levels:
         rec, u, K = level_record(make, L, tol=tol, precision=precision, **solve_kw)
+        rec["err_l2"], rec["err_energy"] = rel(u_ref - interpolate(u, q, L, ref_level), u_ref, K_ref)
         ur = interpolate(u_ref, q, ref_level, L)
-        e = u - ur
-        Ke = qtt_fe_apply(K, e)
-        Kur = qtt_fe_apply(K, ur)
-        rec["err_l2"] = float(torch.linalg.norm(e) / torch.linalg.norm(ur))
-        rec["err_energy"] = float(torch.sqrt(torch.clamp(torch.dot(e, Ke), min=0.0)) /
-                                  torch.sqrt(torch.dot(ur, Kur)))
+        rec["err_l2_nodal"], rec["err_energy_nodal"] = rel(u - ur, ur, K)
         out.append(rec)
     ref_rec["reference"] = True
     out.append(ref_rec)
@@ -107,7 +114,7 @@ def rates(records: List[Dict]) -> Dict[str, float]:
         return {}
     lh = np.log([1.0 / ((1 << r["d"]) - 1) for r in rs])
     out = {}
-    for key in ("err_l2", "err_energy"):
+    for key in ("err_l2", "err_energy", "err_l2_nodal", "err_energy_nodal"):
         ly = np.log([r[key] for r in rs])
         out["order_" + key] = float(np.polyfit(lh, ly, 1)[0])
     nd = np.asarray([r["N_d"] for r in rs], dtype=float)

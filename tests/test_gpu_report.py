@@ -44,8 +44,9 @@ def test_fe_apply_matches_oracle_system(make, L):
 
 
 def test_level_study_orders_and_counts():
-    """Smooth manufactured solution (fully clamped plate): the Q1 orders
-    hold; a clamped-free corner (the cantilever plates) lowers both."""
+    """Smooth manufactured solution (fully clamped plate): the field error
+    falls as h^2 in L2 and h in energy (Q1); a clamped-free corner (the
+    cantilever plates) lowers both."""
     recs = report.study(W.plate_manufactured, [4, 5, 6, 7], ref_level=10, tol=1e-10)
     lv = [r for r in recs if "err_l2" in r]
     e2 = [r["err_l2"] for r in lv]
@@ -54,6 +55,10 @@ def test_level_study_orders_and_counts():
     rt = report.rates(recs)
     assert 1.7 <= rt["order_err_l2"] <= 2.3, rt
     assert 0.8 <= rt["order_err_energy"] <= 1.2, rt
+    # the nodal difference to the interpolated reference is superconvergent
+    # on uniform Q1 meshes: O(h^2) in the discrete energy norm as well
+    assert 1.7 <= rt["order_err_l2_nodal"] <= 2.3, rt
+    assert 1.7 <= rt["order_err_energy_nodal"] <= 2.3, rt
     for r in recs:
         ranks = r["ranks"]
         assert r["R_d"] == max(ranks)
