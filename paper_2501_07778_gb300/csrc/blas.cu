@@ -220,9 +220,11 @@ void gemm(cudaStream_t s, bool tA, bool tB, int M, int N, int K, T alpha, const 
   const long long tiles = (long long)((M + GBM - 1) / GBM) * ((N + GBN - 1) / GBN) * batch;
   const long long two_waves = 2LL * num_sms();
   int splits = 1;
-  if (tiles < two_waves && K >= 256) {
+  // (FP64 runs at about 7 GFLOP/s per SM on this GPU: a GEMM whose tiles
+  // leave SMs idle is worth splitting down to 32-deep K chunks)
+  if (tiles < two_waves && K >= 64) {
     long long want = (two_waves + tiles - 1) / tiles;
-    splits = (int)std::min<long long>(want, (K + 127) / 128);
+    splits = (int)std::min<long long>(want, (K + 31) / 32);
     splits = std::max(1, std::min(splits, 65535 / std::max(1, batch)));
   }
   int kchunk = K;
@@ -552,9 +554,9 @@ bool plan_contract(const char* spec, const int* dA, const int* dB, int sizeof_T,
   ca.tiles_n = (int)((nFB + CT_BN - 1) / CT_BN);
   const long long tiles = (long long)ca.tiles_m * ca.tiles_n * nBt;
   int splits = 1;
-  if (tiles < min_items && nK >= 256) {
+  if (tiles < min_items && nK >= 64) {
     long long want = (min_items + tiles - 1) / tiles;
-    splits = (int)std::min<long long>(want, (nK + 127) / 128);
+    splits = (int)std::min<long long>(want, (nK + 31) / 32);
     splits = std::max(1, splits);
   }
   int kchunk = (int)std::max<long long>(1, nK);
