@@ -16,7 +16,7 @@
 namespace qtt {
 namespace {
 
-constexpr int NB = 32;         // panel width
+constexpr int NB = 16;         // panel width (a panel runs on one SM: its N nb^2 FP64 work grows with nb)
 constexpr size_t kJacobiSmem = 200 * 1024;   // dynamic shared memory of the in-smem Jacobi sweeps
 constexpr int PT = 1024;       // panel kernel threads
 
@@ -243,8 +243,10 @@ __device__ int jacobi_body(int m, int n, T* W, int ldw, T* Vm, int ldv, int max_
 // run on up to np/2 SMs instead of one; a grid barrier separates the rounds.
 // Column data written in one round is read by other SMs in the next, so the
 // loads bypass L1 (__ldcg).  rot[s] counts the warps that rotated in sweep s
-// (zeroed by the host); every thread reads it after the sweep's last
-// barrier, so all CTAs take the same stop decision.  Cooperative launch only.
+// (zeroed by the host) and rot[max_sweeps + s] the warps with a rotation
+// above the quadratic-convergence threshold; every thread reads them after
+// the sweep's last barrier, so all CTAs take the same stop decision.
+// Cooperative launch only.
 // ---------------------------------------------------------------------------
 template <typename T, typename Acc>
 __global__ void jacobi_coop_kernel(int m, int n, T* W, int ldw, T* Vm, int ldv, int max_sweeps, unsigned* rot,
@@ -258,8 +260,12 @@ __global__ void jacobi_coop_kernel(int m, int n, T* W, int ldw, T* Vm, int ldv, 
   const Acc tol = (Acc)(1e-15 * (double)(m > 1 ? m : 1));
   const Acc tolf = (sizeof(T) == 4) ? (Acc)(1e-7 * (double)(m > 1 ? m : 1)) : tol;
   int sweep = 0;
+  // a sweep whose rotations are all tiny (relative off-diagonal below
+  // 1e-8 in FP64) leaves the columns orthogonal to working accuracy
+  // (quadratic convergence), so it ends the sweeps without a confirming one
+  const Acc big = (sizeof(T) == 8) ? (Acc)1e-8 : (Acc)1e-4;
   for (; sweep < max_sweeps; ++sweep) {
-    bool any = false;
+    bool any = false, large = false;
     for (int round = 0; round < np - 1; ++round) {
       for (int pi = gw; pi < np / 2; pi += nwarps) {
         int p, q;
@@ -285,6 +291,7 @@ __global__ void jacobi_coop_kernel(int m, int n, T* W, int ldw, T* Vm, int ldv, 
         be = wsum(be);
         ga = wsum(ga);
         if (ga == (Acc)0 || !(fabs(ga) > tolf * sqrt(al * be))) continue;
+        if (fabs(ga) > big * sqrt(al * be)) large = true;
         Acc zeta = (be - al) / ((Acc)2 * ga);
         Acc t = (zeta >= (Acc)0 ? (Acc)1 : (Acc)-1) / (fabs(zeta) + sqrt((Acc)1 + zeta * zeta));
         Acc cs = (Acc)1 / sqrt((Acc)1 + t * t), sn = cs * t;
@@ -305,8 +312,13 @@ __global__ void jacobi_coop_kernel(int m, int n, T* W, int ldw, T* Vm, int ldv, 
       grid.sync();
     }
     if (any && lane == 0) atomicAdd(&rot[sweep], 1u);
+    if (large && lane == 0) atomicAdd(&rot[max_sweeps + sweep], 1u);
     grid.sync();
     if (*(volatile unsigned*)&rot[sweep] == 0u) break;
+    if (*(volatile unsigned*)&rot[max_sweeps + sweep] == 0u) {
+      ++sweep;
+      break;
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0 && sweeps_out) *sweeps_out = sweep;
 }
@@ -477,8 +489,8 @@ void jacobi_sweeps(cudaStream_t s, Arena& ar, int m, int n, T* W, int ldw, T* Vm
   int occ = 0;
   QTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_coop_kernel<T, Acc>, 32 * wpb, 0));
   const int grid = std::max(1, std::min((pairs + wpb - 1) / wpb, sms * std::max(1, occ)));
-  unsigned* rot = ar.alloc<unsigned>(max_sweeps);
-  QTT_CUDA(cudaMemsetAsync(rot, 0, sizeof(unsigned) * max_sweeps, s));
+  unsigned* rot = ar.alloc<unsigned>(2 * max_sweeps);   // rotations, large rotations per sweep
+  QTT_CUDA(cudaMemsetAsync(rot, 0, sizeof(unsigned) * 2 * max_sweeps, s));
   int* none = nullptr;
   void* args[] = {&m, &n, &W, &ldw, &Vm, &ldv, &max_sweeps, &rot, &none};
   QTT_CUDA(cudaLaunchCooperativeKernel((void*)jacobi_coop_kernel<T, Acc>, grid, 32 * wpb, args, 0, s));
