@@ -89,6 +89,9 @@ def parse(argv=None):
     ap.add_argument("--train-steps", type=int, default=400)
     ap.add_argument("--warm-start", action="store_true",
                     help="fast form with the learned warm start (8 basis solves + MLP training before timing)")
+    ap.add_argument("--superposition-start", action="store_true",
+                    help="fast form warm-started by superposing stored method solutions interpolated in nu "
+                         "(basis solves before timing)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-L", type=int, default=6, help="level of the complete oracle solves (CPU legs)")
     ap.add_argument("--cpu-solves", type=int, default=3, help="timed oracle solves of the cpu_baseline leg")
@@ -442,6 +445,16 @@ def main(argv=None):
     if args.form == "fast" and args.warm_start:
         net, ws_info = train_warm_start(args.L, args.tol, args.train_steps)
         log(f"warm start ready: {ws_info}")
+    elif args.form == "fast" and args.superposition_start:
+        from paper_2501_07778_gb300 import warmstart as ws
+        t0 = time.perf_counter()
+        nus = tuple(np.linspace(0.2, 0.45, 7))
+        net = ws.SuperpositionStart(args.L, nus, order=3, tol=args.tol, precision=q.QTT_MIXED, kick_rank=KICK_RANK,
+                                    max_sweeps=MAX_SWEEPS)
+        ws_info = {"kind": "superposition of stored method solutions (2 unit tractions x 7 nu values), "
+                           "Lagrange interpolation in nu over the 3 nearest", "basis_solves": 2 * len(nus),
+                   "basis_s": round(time.perf_counter() - t0, 2), "used": True}
+        log(f"superposition start ready: {ws_info}")
 
     def step_slice(st):
         return P[st * batch:(st + 1) * batch], probs[st * batch:(st + 1) * batch]
@@ -556,7 +569,8 @@ def main(argv=None):
             "data": "synthetic",
             "config": {"workload": workload_name(args.L), "form": args.form, "L": args.L,
                        "batch_per_rank": batch, "workers": args.workers if batch > 1 else 1,
-                       "learned_warm_start": ws_info is not None and bool(ws_info.get("used")),
+                       "learned_warm_start": bool(args.warm_start) and ws_info is not None and bool(ws_info.get("used")),
+                       "superposition_start": bool(args.superposition_start),
                        "accept_rel_residual": args.tol, "kick_rank": args.kick_rank, "max_sweeps": args.max_sweeps,
                        "tensor_cores": {0: "autotuned", 1: "always"}.get(args.tensor_cores, "off"),
                        "l2": "flushed (256 MB write) before every timed step"},

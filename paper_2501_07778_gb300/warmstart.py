@@ -191,3 +191,52 @@ def train(net: WarmStartMLP, basis: List[QTT], P: np.ndarray, coef: np.ndarray, 
         a = lr * (0.1 ** (st / max(1, steps - 1)))
         losses.append(net.train_step(P[idx], basis, coef[idx], lr=a, gram=gram))
     return losses
+
+
+class SuperpositionStart:
+    """Non-learned warm start for the plate family: the plane-stress
+    solution is linear in the traction and in 1/E, and smooth in nu, so
+    stored method solutions of the two unit tractions on a nu grid give
+
+        x0 = (amp / E) * sum_j w_j(nu) (cos(theta) U_x(nu_j) + sin(theta) U_y(nu_j)),
+
+    with w_j the Lagrange weights of the `order` grid points nearest to nu
+    (exact at grid points).  The sum is formed and rounded by the library's
+    qtt_axpby / qtt_round.  Its residual is of the size of the interpolation
+    error in nu (a smooth field), unlike a rank-limited learned start whose
+    error reaches the high frequencies that K amplifies."""
+
+    def __init__(self, L: int, nus: Sequence[float], order: int = 3, tol: float = 1e-8, round_tol: float = 1e-9,
+                 **solve_kw):
+        self.nus = np.asarray(sorted(nus), dtype=float)
+        self.order = max(1, min(order, len(self.nus)))
+        self.round_tol = round_tol
+        self.basis = basis_solutions(L, list(self.nus), tol=tol, **solve_kw)   # U_x(nu_0), U_y(nu_0), ...
+
+    def weights(self, nu: float):
+        """Indices and Lagrange weights of the nearest `order` grid points."""
+        idx = np.argsort(np.abs(self.nus - nu))[:self.order]
+        idx = np.sort(idx)
+        xs = self.nus[idx]
+        w = []
+        for a, xa in enumerate(xs):
+            p = 1.0
+            for b, xb in enumerate(xs):
+                if b != a:
+                    p *= (nu - xb) / (xa - xb)
+            w.append(p)
+        return idx, np.asarray(w)
+
+    def predict(self, params: np.ndarray) -> List[QTT]:
+        from . import qtt_axpby, qtt_round
+        out = []
+        for E, nu, amp, th in params:
+            idx, w = self.weights(float(nu))
+            x = None
+            for j, wj in zip(idx, w):
+                cx, cy = float(wj * math.cos(th) * amp / E), float(wj * math.sin(th) * amp / E)
+                term = qtt_axpby(cx, self.basis[2 * j], cy, self.basis[2 * j + 1])
+                x = term if x is None else qtt_axpby(1.0, x, 1.0, term)
+                qtt_round(x, self.round_tol)
+            out.append(x)
+        return out

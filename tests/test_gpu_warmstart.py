@@ -110,3 +110,30 @@ def test_trained_warm_start_beats_cold_start():
         warm += iw["sweeps"]
         cold += ic["sweeps"]
     assert warm < cold, (warm, cold)
+
+
+def test_superposition_start_is_accurate_in_the_residual():
+    """The non-learned start (stored unit-traction solutions interpolated in
+    nu, scaled by amp / E) has a small relative residual, the solve from it
+    reaches the sparse direct solution, and it needs fewer sweeps than a
+    cold start."""
+    import workloads as W
+    from oracle import fem
+    from paper_2501_07778_gb300 import warmstart as ws
+    L = 7
+    ss = ws.SuperpositionStart(L, (0.2, 0.3, 0.4, 0.45), order=3, tol=1e-10, precision=q.QTT_MIXED, kick_rank=8)
+    P = W.plate_params(2, 3)
+    x0s = ss.predict(P)
+    for (E, nu, amp, th), x0 in zip(P, x0s):
+        prob = W.plate_top_traction(L, float(E), float(nu), float(amp), float(th))
+        K, f = q.qtt_assemble_stiffness(prob)
+        r0 = q.qtt_residual_fe(K, x0, f)
+        assert r0 <= 0.05, r0
+        u, info = q.qtt_solve(K, f, x0=x0, tol=1e-9, precision=q.QTT_MIXED, kick_rank=8, max_sweeps=30)
+        uc, ic = q.qtt_solve(K, f, tol=1e-9, precision=q.QTT_MIXED, kick_rank=8, max_sweeps=30)
+        assert info["rc"] == 0 and ic["rc"] == 0
+        assert info["sweeps"] <= ic["sweeps"], (info["sweeps"], ic["sweeps"])
+        um, nm = fem.solve_merged(prob)
+        ref = fem.merged_to_qtt(prob, um, nm)
+        ug = q.qtt_to_full(u).cpu().numpy()
+        assert np.linalg.norm(ug - ref) / np.linalg.norm(ref) <= 1e-7
