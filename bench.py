@@ -16,9 +16,13 @@ back into host memory (the e2e object), measured in the same loop.
 
 Forms:
   --form fast   (default) mixed precision: FP64 interfaces and residuals,
-                FP32 Krylov operators, FP64 outer refinement; with
+                FP32 Krylov operators (tensor cores where the autotuner
+                finds them faster), FP64 outer refinement; with
                 --warm-start also the learned warm start (MLP inference;
-                the network is trained before the timed region)
+                the network is trained before the timed region), with
+                --superposition-start the start formed from stored method
+                solutions interpolated in nu (solved before the timed
+                region; the interpolation runs inside every timed step)
   --form plain  FP64 AMEn, cold start, one solve at a time
 The fast-form line also carries a `plain` object: the plain form timed on
 the first `--plain-solves` problems of the same workload after the timed
