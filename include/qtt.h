@@ -220,7 +220,9 @@ typedef struct {
   int kick_rank;          /* residual-proxy rank rho used for enrichment (<= 0: 4) */
   int max_sweeps;         /* per AMEn run (<= 0: 30) */
   int local_direct_max;   /* local systems up to this size use dense LU (<= 0: 2048) */
-  int local_restart;      /* GMRES restart length for larger local systems (<= 0: 40) */
+  int local_restart;      /* Krylov iterations per cycle of the larger local
+                             systems (<= 0: 40; GMRES at most 64, CG at most
+                             1000); every cycle starts from an FP64 residual */
   int local_max_cycles;   /* GMRES restart cycles per local solve (<= 0: 8) */
   int precision;          /* QTT_F64, QTT_F32 or QTT_MIXED */
   int refine_max;         /* QTT_F64 / QTT_MIXED: maximum outer refinement steps

@@ -550,6 +550,7 @@ struct Amen {
   int D;
   double tol;
   int max_rank, kick, max_sweeps, ndir, restart, cycles, verbose;
+  int cg_iters = 40;          // CG iterations per cycle (GMRES keeps restart <= 64)
   bool mixed_local = false;   // FP32 operator inside the local GMRES cycles
   bool tensor_cores = false;  // the FP32 local operator on tcgen05 (3xTF32) at ranks >= 32
   bool tc_always = false;     // ... in every bucket, not only where the autotuner found it faster
@@ -779,7 +780,7 @@ struct Amen {
   double cg(int k, const T* PhiL, int r0, const T* PhiR, int r1, const T* g, double gn, T* xk, double rtol) {
     const int n = A->n[k], R0 = rA(k), R1 = rA(k + 1);
     const int N = r0 * n * r1;
-    const int m = std::max(1, restart);
+    const int m = std::max(1, cg_iters);
     Arena sc(s);
     const U* PL = reinterpret_cast<const U*>(PhiL);
     const U* PR = reinterpret_cast<const U*>(PhiR);
@@ -1281,7 +1282,8 @@ int amen_run(cudaStream_t s, const qtt_tensor* K, const qtt_tensor* f, qtt_tenso
   am.kick = z->r[1];
   am.max_sweeps = o.max_sweeps > 0 ? o.max_sweeps : 30;
   am.ndir = o.local_direct_max > 0 ? o.local_direct_max : 2048;
-  am.restart = std::min(o.local_restart > 0 ? o.local_restart : 40, 64);
+  am.restart = std::min(o.local_restart > 0 ? o.local_restart : 40, 64);   // GMRES Hessenberg storage
+  am.cg_iters = std::min(o.local_restart > 0 ? o.local_restart : 40, 1000);
   am.cycles = o.local_max_cycles > 0 ? o.local_max_cycles : 20;
   am.verbose = o.verbose;
   am.info = info;

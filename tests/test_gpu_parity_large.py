@@ -90,7 +90,7 @@ def test_config2_plate_L10_fp64_full_vector():
     error of the whole displacement vector against sparse direct <= 1e-8."""
     prob = W.plate_traction_smooth(10)
     K, f = q.qtt_assemble_stiffness(prob)
-    u, info = q.qtt_solve(K, f, tol=1e-10, precision=q.QTT_F64, kick_rank=8, max_sweeps=24, refine_max=4)
+    u, info = q.qtt_solve(K, f, tol=1e-10, precision=q.QTT_F64, kick_rank=8, max_sweeps=24)
     ug = q.qtt_to_full(u).cpu().numpy()
     del u
     ref = _merged_in_qtt_order(prob)
