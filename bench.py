@@ -394,6 +394,8 @@ def roofline_of(prof, peaks, sms):
                    "launches": int(v[3])} for k, v in prof.items()}
     return {"bound": bound, "kernel": dom, "achieved": round(achieved, 4), "peak": round(peak, 3) if peak else None,
             "unit": unit, "frac": round(achieved / peak, 5) if peak else None, "traffic": None,
+            "traffic_note": "null: the dominant kernels' operands are L2-resident and a solve's launches of them are "
+                            "too many for an ncu capture; single-launch ncu captures in profiles/",
             "launches": int(n), "avg_launch_us": round(1e3 * ms / max(1, n), 2), "peak_source": src,
             "sms": sms, "classes": classes,
             "note": "per-class CUDA events bracket every launch of the timed steps on its own stream; "
