@@ -11,48 +11,50 @@
 namespace qtt {
 
 // ---------------------------------------------------------------------------
-// GEMM: 64x64 output tile per 256-thread block, 16-deep K slices staged in
-// shared memory, 4x4 register tile per thread (rows tx + 16 i, cols ty + 16 j
+// GEMM: TS x TS output tile per 256-thread block (TS = 64, or 32 when 64 x 64
+// tiles cannot fill the SMs), 16-deep K slices staged in shared memory,
+// (TS/16) x (TS/16) register tile per thread (rows tx + 16 i, cols ty + 16 j
 // so that shared-memory reads are conflict-free).
 // ---------------------------------------------------------------------------
 namespace {
-constexpr int GBM = 64, GBN = 64, GBK = 16;
+constexpr int GBM = 64, GBK = 16;
 
 // gridDim.z = batch * splits: a split computes the partial product over
 // K range [split * kchunk, min(K, (split + 1) * kchunk)) and, when splits > 1,
 // adds alpha * partial into C atomically (C pre-scaled by beta on the host side).
-template <typename T>
+template <typename T, int TS>
 __global__ void __launch_bounds__(256) gemm_kernel(bool tA, bool tB, int M, int N, int K, T alpha, const T* __restrict__ A,
                                                   int lda, long long sA, const T* __restrict__ B, int ldb,
                                                   long long sB, T beta, T* __restrict__ C, int ldc, long long sC,
                                                   int splits, int kchunk) {
-  __shared__ T As[GBK][GBM + 1];
-  __shared__ T Bs[GBK][GBN + 1];
+  constexpr int R = TS / 16, LOADS = GBK * TS / 256;
+  __shared__ T As[GBK][TS + 1];
+  __shared__ T Bs[GBK][TS + 1];
   const int bz = blockIdx.z / splits, sp = blockIdx.z % splits;
   A += bz * sA;
   B += bz * sB;
   C += bz * sC;
   const int kb = sp * kchunk, ke = min(K, kb + kchunk);
-  const int m0 = blockIdx.x * GBM, n0 = blockIdx.y * GBN;
+  const int m0 = blockIdx.x * TS, n0 = blockIdx.y * TS;
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  T acc[4][4];
+  T acc[R][R];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < R; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    for (int j = 0; j < R; ++j) acc[i][j] = T(0);
   for (int k0 = kb; k0 < ke; k0 += GBK) {
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
+    for (int t = 0; t < LOADS; ++t) {
       int L = tid + 256 * t;
       int i, k;
-      if (!tA) { i = L % GBM; k = L / GBM; } else { k = L % GBK; i = L / GBK; }
+      if (!tA) { i = L % TS; k = L / TS; } else { k = L % GBK; i = L / GBK; }
       int gi = m0 + i, gk = k0 + k;
       T v = T(0);
       if (gi < M && gk < ke) v = tA ? A[gk + (long long)gi * lda] : A[gi + (long long)gk * lda];
       As[k][i] = v;
       int j, kk;
-      if (!tB) { kk = L % GBK; j = L / GBK; } else { j = L % GBN; kk = L / GBN; }
+      if (!tB) { kk = L % GBK; j = L / GBK; } else { j = L % TS; kk = L / TS; }
       int gj = n0 + j, gk2 = k0 + kk;
       T w = T(0);
       if (gj < N && gk2 < ke) w = tB ? B[gj + (long long)gk2 * ldb] : B[gk2 + (long long)gj * ldb];
@@ -61,24 +63,24 @@ __global__ void __launch_bounds__(256) gemm_kernel(bool tA, bool tB, int M, int 
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < GBK; ++k) {
-      T a[4], b[4];
+      T a[R], b[R];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[k][tx + 16 * i];
+      for (int i = 0; i < R; ++i) a[i] = As[k][tx + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[k][ty + 16 * j];
+      for (int j = 0; j < R; ++j) b[j] = Bs[k][ty + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < R; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < R; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < R; ++i) {
     int gi = m0 + tx + 16 * i;
     if (gi >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < R; ++j) {
       int gj = n0 + ty + 16 * j;
       if (gj >= N) continue;
       T* c = C + gi + (long long)gj * ldc;
@@ -104,13 +106,14 @@ __global__ void scale_matrix_kernel(int M, int N, T* C, int ldc, long long sC, i
 // Small-K / skinny fallback is not needed: the tile kernel handles any shape.
 
 // Work-item loop over the strided contraction (contract.cuh): one block per
-// output tile (and K split), grid-strided.
-template <typename T>
+// TS x TS output tile (and K split), grid-strided.
+template <typename T, int TS>
 __global__ void __launch_bounds__(256) contract_kernel(ContractArgs a, T alpha, const T* __restrict__ A,
                                                        const T* __restrict__ B, T beta, T* __restrict__ C,
                                                        long long items) {
-  __shared__ ContractSmem<T> sm;
-  for (long long it = blockIdx.x; it < items; it += gridDim.x) contract_tile<T>(a, alpha, A, B, beta, C, (int)it, sm);
+  __shared__ ContractSmem<T, TS> sm;
+  for (long long it = blockIdx.x; it < items; it += gridDim.x)
+    contract_tile<T, TS>(a, alpha, A, B, beta, C, (int)it, sm);
 }
 
 // C = beta C over the strided output (before split-K accumulation)
@@ -216,12 +219,14 @@ void gemm(cudaStream_t s, bool tA, bool tB, int M, int N, int K, T alpha, const 
     }
     return;
   }
-  // split K when the output tiles alone cannot fill the SMs twice over
-  const long long tiles = (long long)((M + GBM - 1) / GBM) * ((N + GBN - 1) / GBN) * batch;
+  // FP64 runs at about 7 GFLOP/s per SM on this GPU: a GEMM whose 64 x 64
+  // tiles leave SMs idle takes 32 x 32 tiles, and is split down to 32-deep K
+  // chunks when even those cannot fill the SMs twice over
   const long long two_waves = 2LL * num_sms();
+  auto tiles_of = [&](int ts) { return (long long)((M + ts - 1) / ts) * ((N + ts - 1) / ts) * batch; };
+  const int TS = (sizeof(T) == 8 && tiles_of(GBM) < two_waves) ? 32 : GBM;
+  const long long tiles = tiles_of(TS);
   int splits = 1;
-  // (FP64 runs at about 7 GFLOP/s per SM on this GPU: a GEMM whose tiles
-  // leave SMs idle is worth splitting down to 32-deep K chunks)
   if (tiles < two_waves && K >= 64) {
     long long want = (two_waves + tiles - 1) / tiles;
     splits = (int)std::min<long long>(want, (K + 31) / 32);
@@ -232,7 +237,7 @@ void gemm(cudaStream_t s, bool tA, bool tB, int M, int N, int K, T alpha, const 
     kchunk = ((K + splits - 1) / splits + GBK - 1) / GBK * GBK;
     splits = (K + kchunk - 1) / kchunk;
   }
-  dim3 grid((M + GBM - 1) / GBM, (N + GBN - 1) / GBN, batch * splits);
+  dim3 grid((M + TS - 1) / TS, (N + TS - 1) / TS, batch * splits);
   QTT_REQUIRE(grid.y <= 65535 && grid.z <= 65535, "gemm grid too large");
   ProfToken pt = prof_begin(sizeof(T) == 8 ? PROF_GEMM_F64 : PROF_GEMM_F32, s);
   if (splits > 1) {
@@ -240,8 +245,12 @@ void gemm(cudaStream_t s, bool tA, bool tB, int M, int N, int K, T alpha, const 
     scale_matrix_kernel<T><<<grid_for(total), 256, 0, s>>>(M, N, C, ldc, sC, batch, beta);
     QTT_CHECK_LAUNCH();
   }
-  gemm_kernel<T><<<grid, 256, 0, s>>>(tA, tB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits,
-                                      kchunk);
+  if (TS == 32)
+    gemm_kernel<T, 32><<<grid, 256, 0, s>>>(tA, tB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits,
+                                            kchunk);
+  else
+    gemm_kernel<T, GBM><<<grid, 256, 0, s>>>(tA, tB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC,
+                                             splits, kchunk);
   QTT_CHECK_LAUNCH();
   if (pt.ev) {
     const double mn = (double)M * N, b = (double)batch;
@@ -397,7 +406,7 @@ void einsum(cudaStream_t s, Arena& ar, const char* spec, const T* A, const int* 
   if (nFA == 0 || nFB == 0 || nBt == 0) return;
   {
     ContractArgs ca{};
-    if (plan_contract(spec, dA, dB, (int)sizeof(T), 2LL * num_sms(), ca)) {
+    if (plan_contract(spec, dA, dB, (int)sizeof(T), 2LL * num_sms(), ca, sizeof(T) == 8)) {
       const long long items = contract_items(ca);
       ProfToken pt = prof_begin(sizeof(T) == 8 ? PROF_GEMM_F64 : PROF_GEMM_F32, s);
       if (ca.splits > 1) {
@@ -405,7 +414,8 @@ void einsum(cudaStream_t s, Arena& ar, const char* spec, const T* A, const int* 
         QTT_CHECK_LAUNCH();
       }
       const int grid = (int)std::min<long long>(items, 1LL << 30);
-      contract_kernel<T><<<grid, 256, 0, s>>>(ca, alpha, A, B, beta, C, items);
+      if (ca.tile == 32) contract_kernel<T, 32><<<grid, 256, 0, s>>>(ca, alpha, A, B, beta, C, items);
+      else contract_kernel<T, CT_BM><<<grid, 256, 0, s>>>(ca, alpha, A, B, beta, C, items);
       QTT_CHECK_LAUNCH();
       if (pt.ev) {
         const double mn = (double)ca.M * ca.N, bt = (double)ca.batch;
@@ -471,7 +481,7 @@ void einsum(cudaStream_t s, Arena& ar, const char* spec, const T* A, const int* 
 // Contraction planner (contract.cuh)
 // ---------------------------------------------------------------------------
 bool plan_contract(const char* spec, const int* dA, const int* dB, int sizeof_T, long long min_items,
-                   ContractArgs& ca) {
+                   ContractArgs& ca, bool allow_small) {
   std::string sp(spec);
   size_t comma = sp.find(','), arrow = sp.find("->");
   QTT_REQUIRE(comma != std::string::npos && arrow != std::string::npos, "contract: bad spec");
@@ -550,9 +560,11 @@ bool plan_contract(const char* spec, const int* dA, const int* dB, int sizeof_T,
   ca.cb = make(batch, sc);
   ca.a_m_fast = (ca.am.s[0] == 1) || !(ca.ak.s[0] == 1);
   ca.b_n_fast = (ca.bn.s[0] == 1) && !(ca.bk.s[0] == 1);
-  ca.tiles_m = (int)((nFA + CT_BM - 1) / CT_BM);
-  ca.tiles_n = (int)((nFB + CT_BN - 1) / CT_BN);
-  const long long tiles = (long long)ca.tiles_m * ca.tiles_n * nBt;
+  auto tiles_of = [&](int ts) { return ((nFA + ts - 1) / ts) * ((nFB + ts - 1) / ts) * nBt; };
+  ca.tile = (allow_small && tiles_of(CT_BM) < min_items) ? 32 : CT_BM;
+  ca.tiles_m = (int)((nFA + ca.tile - 1) / ca.tile);
+  ca.tiles_n = (int)((nFB + ca.tile - 1) / ca.tile);
+  const long long tiles = tiles_of(ca.tile);
   int splits = 1;
   if (tiles < min_items && nK >= 64) {
     long long want = (min_items + tiles - 1) / tiles;

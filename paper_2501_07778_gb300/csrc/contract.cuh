@@ -24,6 +24,7 @@ struct ContractArgs {
   int M, N, K, batch;
   IdxMap am, ak, bk, bn, cm, cn, ab, bb, cb;
   bool a_m_fast, b_n_fast;   // which logical index runs along stride-1 memory
+  int tile;                  // square output tile side (64, or 32 for small contractions)
   int tiles_m, tiles_n;      // output tiles per batch entry
   int splits, kchunk;        // K split (splits > 1: atomic accumulation into C)
 };
@@ -40,18 +41,22 @@ __device__ __forceinline__ long long idx_off(const IdxMap& d, int idx) {
   return o;
 }
 
-template <typename T>
+template <typename T, int TS = CT_BM>
 struct ContractSmem {
-  T As[CT_BK][CT_BM + 1];
-  T Bs[CT_BK][CT_BN + 1];
-  long long rowA[CT_BM], colB[CT_BN], kA[CT_BK], kB[CT_BK];
+  T As[CT_BK][TS + 1];
+  T Bs[CT_BK][TS + 1];
+  long long rowA[TS], colB[TS], kA[CT_BK], kB[CT_BK];
 };
 
-// One 64 x 64 output tile of work item `item` (tile_m, tile_n, batch, split
-// flattened); all 256 threads of the block participate.
-template <typename T>
+// One TS x TS output tile (TS = 64, or 32 for contractions too small to fill
+// the SMs with 64 x 64 tiles) of work item `item` (tile_m, tile_n, batch,
+// split flattened); all 256 threads of the block participate, each holding a
+// (TS/16) x (TS/16) register tile.
+template <typename T, int TS = CT_BM>
 __device__ void contract_tile(const ContractArgs& a, T alpha, const T* __restrict__ A, const T* __restrict__ B, T beta,
-                              T* __restrict__ C, int item, ContractSmem<T>& sm) {
+                              T* __restrict__ C, int item, ContractSmem<T, TS>& sm) {
+  constexpr int R = TS / 16;                     // outputs per thread along each side
+  constexpr int LOADS = (CT_BK * TS + 255) / 256;
   const int tm = item % a.tiles_m;
   int rest = item / a.tiles_m;
   const int tn = rest % a.tiles_n;
@@ -62,32 +67,33 @@ __device__ void contract_tile(const ContractArgs& a, T alpha, const T* __restric
   B += idx_off(a.bb, bz);
   C += idx_off(a.cb, bz);
   const int kb = sp * a.kchunk, ke = min(a.K, kb + a.kchunk);
-  const int m0 = tm * CT_BM, n0 = tn * CT_BN;
+  const int m0 = tm * TS, n0 = tn * TS;
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   __syncthreads();
-  if (tid < CT_BM) sm.rowA[tid] = (m0 + tid < a.M) ? idx_off(a.am, m0 + tid) : 0;
-  else if (tid < CT_BM + CT_BN) sm.colB[tid - CT_BM] = (n0 + tid - CT_BM < a.N) ? idx_off(a.bn, n0 + tid - CT_BM) : 0;
-  T acc[4][4];
+  if (tid < TS) sm.rowA[tid] = (m0 + tid < a.M) ? idx_off(a.am, m0 + tid) : 0;
+  else if (tid < 2 * TS) sm.colB[tid - TS] = (n0 + tid - TS < a.N) ? idx_off(a.bn, n0 + tid - TS) : 0;
+  T acc[R][R];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < R; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    for (int j = 0; j < R; ++j) acc[i][j] = T(0);
   for (int k0 = kb; k0 < ke; k0 += CT_BK) {
     __syncthreads();
     if (tid < CT_BK) sm.kA[tid] = (k0 + tid < ke) ? idx_off(a.ak, k0 + tid) : 0;
     else if (tid < 2 * CT_BK) sm.kB[tid - CT_BK] = (k0 + tid - CT_BK < ke) ? idx_off(a.bk, k0 + tid - CT_BK) : 0;
     __syncthreads();
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
+    for (int t = 0; t < LOADS; ++t) {
       int L = tid + 256 * t;
+      if (L >= CT_BK * TS) break;
       int i, k;
-      if (a.a_m_fast) { i = L % CT_BM; k = L / CT_BM; } else { k = L % CT_BK; i = L / CT_BK; }
+      if (a.a_m_fast) { i = L % TS; k = L / TS; } else { k = L % CT_BK; i = L / CT_BK; }
       T v = T(0);
       if (m0 + i < a.M && k0 + k < ke) v = A[sm.rowA[i] + sm.kA[k]];
       sm.As[k][i] = v;
       int j, kk;
-      if (a.b_n_fast) { j = L % CT_BN; kk = L / CT_BN; } else { kk = L % CT_BK; j = L / CT_BK; }
+      if (a.b_n_fast) { j = L % TS; kk = L / TS; } else { kk = L % CT_BK; j = L / CT_BK; }
       T w = T(0);
       if (n0 + j < a.N && k0 + kk < ke) w = B[sm.kB[kk] + sm.colB[j]];
       sm.Bs[kk][j] = w;
@@ -95,24 +101,24 @@ __device__ void contract_tile(const ContractArgs& a, T alpha, const T* __restric
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < CT_BK; ++k) {
-      T x[4], y[4];
+      T x[R], y[R];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) x[i] = sm.As[k][tx + 16 * i];
+      for (int i = 0; i < R; ++i) x[i] = sm.As[k][tx + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) y[j] = sm.Bs[k][ty + 16 * j];
+      for (int j = 0; j < R; ++j) y[j] = sm.Bs[k][ty + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < R; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(x[i], y[j], acc[i][j]);
+        for (int j = 0; j < R; ++j) acc[i][j] = fma(x[i], y[j], acc[i][j]);
     }
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < R; ++i) {
     const int gi = m0 + tx + 16 * i;
     if (gi >= a.M) continue;
     const long long ro = idx_off(a.cm, gi);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < R; ++j) {
       const int gj = n0 + ty + 16 * j;
       if (gj >= a.N) continue;
       T* c = C + ro + idx_off(a.cn, gj);
@@ -131,10 +137,12 @@ __device__ __forceinline__ long long contract_out_off(const ContractArgs& a, lon
 }
 
 // Host planner: parses "ab,bc->ac" style specs, classifies labels, builds
-// the index maps and chooses the K split (min_items: target number of work
-// items).  Returns false if a label group needs more than four indices.
+// the index maps and chooses the tile (32 x 32 when allow_small and 64 x 64
+// tiles would leave work items below min_items) and the K split (min_items:
+// target number of work items).  Returns false if a label group needs more
+// than four indices.
 bool plan_contract(const char* spec, const int* dA, const int* dB, int sizeof_T, long long min_items,
-                   ContractArgs& ca);
+                   ContractArgs& ca, bool allow_small = false);
 
 __host__ __device__ inline long long contract_items(const ContractArgs& a) {
   return (long long)a.tiles_m * a.tiles_n * a.splits * a.batch;
