@@ -268,8 +268,12 @@ typedef struct {
  * with QTT_MIXED their Krylov cycles apply an FP32 copy of the local
  * operator while interfaces, residuals and truncations stay FP64.  With
  * QTT_F64 / QTT_MIXED, sweeps that stall above tol hand over to outer
- * iterative refinement: the residual f - K u is formed by the FP64 QTT
- * matvec and rounded in FP64 (qtt_round_residual), K d = r is solved the
+ * iterative refinement: the residual f - K u is formed in FP64 and
+ * compressed -- element by element and TT-SVD-rounded (qtt_residual_fe_tt,
+ * rank <= 128) when K comes from qtt_assemble_stiffness and the relative
+ * residual is below 1e-9, where forming it inside the QTT cores loses its
+ * low-frequency part to cancellation; otherwise by the QTT matvec with
+ * randomized FP64 rounding (qtt_round_residual) -- K d = r is solved the
  * same way to inner_tol, and u <- round(u + d).  QTT_F32 runs everything in
  * FP32 without refinement.  Creates *x; info may be NULL.  Returns
  * QTT_ENOCONV (with *x valid) if max_sweeps / refine_max run out. */
@@ -308,6 +312,22 @@ int qtt_residual(const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* f,
  * synchronises the stream. */
 int qtt_residual_fe(const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* f,
                     double* out, void* stream);
+
+/* The residual r = f - K u of qtt_residual_fe as a QTT vector: formed
+ * element by element in FP64 with the same operator (no QTT arithmetic, so
+ * no cancellation between f and K u inside the cores), reordered to QTT
+ * order and compressed by a left-to-right TT-SVD (Section 2's rounding
+ * applied to a full vector): every unfolding drops a tail
+ * <= eps ||r|| / sqrt(d - 1), ranks <= max_rank.  eps in [1e-6, 1) (wide
+ * unfoldings go through their Gram matrix, whose small eigenvectors are
+ * accurate to ~1e-16 (sigma_1 / sigma_k)^2); max_rank >= 1.  *r is a new
+ * FP64 MPS with left-orthonormal cores, owned by the caller (free with
+ * qtt_free); *rel (may be NULL) = ||r|| / ||f|| before compression.
+ * K must come from qtt_assemble_stiffness (QTT_EINVAL otherwise).  This is
+ * the right-hand side of qtt_solve's outer refinement for such K.  Takes
+ * device scratch of a few full vectors; synchronises the stream. */
+int qtt_residual_fe_tt(const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* f,
+                       double eps, int max_rank, qtt_tensor** r, double* rel, void* stream);
 
 /* y = K x with the assembled operator applied as its finite-element stencil
  * (the operator of qtt_residual_fe, masks and concatenation rows included)

@@ -19,7 +19,7 @@ from ._lib import (QTT_F32, QTT_F64, QTT_MIXED, QTT_ORDER_CANONICAL, QTT_ORDER_Z
                    QttSolveOpts)
 
 __all__ = ["QTT", "QttError", "qtt_assemble_stiffness", "qtt_matvec", "qtt_round", "qtt_solve", "qtt_to_full",
-           "qtt_axpby", "qtt_norm", "qtt_residual", "qtt_residual_fe", "qtt_fe_apply", "qtt_round_residual", "qtt_to_full_noalloc", "QTT_F64", "QTT_F32", "QTT_MIXED", "QTT_ORDER_Z_BLOCK",
+           "qtt_axpby", "qtt_norm", "qtt_residual", "qtt_residual_fe", "qtt_residual_fe_tt", "qtt_fe_apply", "qtt_round_residual", "qtt_to_full_noalloc", "QTT_F64", "QTT_F32", "QTT_MIXED", "QTT_ORDER_Z_BLOCK",
            "QTT_ORDER_CANONICAL", "lib"]
 
 
@@ -196,6 +196,16 @@ def qtt_residual_fe(K: QTT, u: QTT, f: QTT, stream=None) -> float:
     v = C.c_double()
     _check(lib().qtt_residual_fe(K.handle, u.handle, f.handle, C.byref(v), _stream(stream)), "qtt_residual_fe")
     return v.value
+
+
+def qtt_residual_fe_tt(K: QTT, u: QTT, f: QTT, eps: float = 1e-3, max_rank: int = 128, stream=None):
+    """f - K u formed element by element (the FE stencil, FP64) and
+    compressed by TT-SVD at relative accuracy eps; returns (r, ||f-Ku||/||f||)."""
+    h = C.c_void_p()
+    rel = C.c_double()
+    _check(lib().qtt_residual_fe_tt(K.handle, u.handle, f.handle, eps, max_rank, C.byref(h), C.byref(rel),
+                                    _stream(stream)), "qtt_residual_fe_tt")
+    return QTT(h), rel.value
 
 
 def qtt_fe_apply(K: QTT, x, out=None, stream=None):

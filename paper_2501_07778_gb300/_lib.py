@@ -67,6 +67,7 @@ SIGNATURES = {
     "qtt_solve": (C.c_int, [P, P, P, P, C.POINTER(QttSolveOpts), PP, C.POINTER(QttSolveInfo), P]),
     "qtt_residual": (C.c_int, [P, P, P, C.POINTER(C.c_double), P]),
     "qtt_residual_fe": (C.c_int, [P, P, P, C.POINTER(C.c_double), P]),
+    "qtt_residual_fe_tt": (C.c_int, [P, P, P, C.c_double, C.c_int, PP, C.POINTER(C.c_double), P]),
     "qtt_fe_apply": (C.c_int, [P, P, P, C.c_size_t, P]),
     "qtt_round_residual": (C.c_int, [P, P, P, C.c_int, C.c_ulonglong, C.POINTER(C.c_double), PP, P]),
     "qtt_solve_batched": (C.c_int, [C.c_int, PP, PP, PP, C.POINTER(QttSolveOpts), C.c_int, PP,

@@ -36,6 +36,19 @@
 namespace qtt {
 double residual64(cudaStream_t s, const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* f);
 bool has_fe_operator(const qtt_tensor* K);
+qtt_tensor* residual_fe_tt(cudaStream_t s, const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* f, double eps,
+                           int max_rank, double* rel);
+// The refinement forms its residual element by element (TT-SVD, ranks
+// <= kFeResidualRank) once the FP64 relative residual is below
+// kFeResidualBelow.  Measured: on the L = 10 plate at 5e-10 the residual
+// formed in QTT arithmetic kept 4 % of K^-1 r, the element-by-element one
+// (rank 128) kept it all and six refinements took the error against sparse
+// direct from 5.2e-9 to 7e-10; on the L = 12 plates at 2-7e-8 the QTT
+// residual reaches 1e-8 in one refinement, while the TT-SVD one is a second
+// slower at rank 128 (FP64 Jacobi SVDs of 512 x 512 Gram matrices) and
+// stalls above 1e-8 at rank 32.
+constexpr int kFeResidualRank = 128;
+constexpr double kFeResidualBelow = 1e-9;
 double residual_fe(cudaStream_t s, const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* u2,
                    const qtt_tensor* f);
 namespace {
@@ -1415,17 +1428,32 @@ int solve(const qtt_tensor* K, const qtt_tensor* f, const qtt_tensor* x0, const 
         Arena ar(s);
         fnorm = norm<double>(s, ar, f);
       }
-      int mr = 1;
-      for (int k = 0; k <= u->d; ++k) mr = std::max(mr, u->r[k]);
-      const int ell = std::min(512, std::max(64, 4 * mr + 16));
-      double kept = 0.0;
-      Tptr r = own(round_residual_rand(s, K, u.get(), f, ell, 0x5eed0000ULL + (unsigned long long)it, &kept));
-      if (o.verbose) {
-        const double full = rel * fnorm, frac = full > 0 ? kept / full : 1.0;
-        fprintf(stderr, "[qtt_solve] refinement %d: residual sketched at rank %d, relative error %.2e\n", it + 1, ell,
-                std::sqrt(std::max(0.0, 1.0 - frac * frac)));
-      }
-      {
+      Tptr r = own(nullptr);
+      if (has_fe_operator(K) && rel <= kFeResidualBelow) {
+        // Near the FP64 floor the residual's low-frequency part -- the one
+        // that carries the error, K^-1 r -- is a small fraction of ||r||
+        // and lost to cancellation when f - K u is formed inside the QTT
+        // cores; formed element by element and TT-SVD-compressed it keeps
+        // it (a rank-16 TT-SVD of the L = 10 plate's residual already
+        // carries all but 3 % of K^-1 r)
+        r = own(residual_fe_tt(s, K, u.get(), f, std::min(1e-2, inner), kFeResidualRank, nullptr));
+        if (o.verbose) {
+          int rr = 1;
+          for (int k = 0; k <= r->d; ++k) rr = std::max(rr, r->r[k]);
+          fprintf(stderr, "[qtt_solve] refinement %d: residual formed in full format, TT-SVD max rank %d\n", it + 1,
+                  rr);
+        }
+      } else {
+        int mr = 1;
+        for (int k = 0; k <= u->d; ++k) mr = std::max(mr, u->r[k]);
+        const int ell = std::min(512, std::max(64, 4 * mr + 16));
+        double kept = 0.0;
+        r = own(round_residual_rand(s, K, u.get(), f, ell, 0x5eed0000ULL + (unsigned long long)it, &kept));
+        if (o.verbose) {
+          const double full = rel * fnorm, frac = full > 0 ? kept / full : 1.0;
+          fprintf(stderr, "[qtt_solve] refinement %d: residual sketched at rank %d, relative error %.2e\n", it + 1,
+                  ell, std::sqrt(std::max(0.0, 1.0 - frac * frac)));
+        }
         Arena ar(s);
         round_tt<double>(s, ar, r.get(), std::min(1e-2, inner), 0);
       }

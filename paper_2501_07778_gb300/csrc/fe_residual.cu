@@ -153,7 +153,8 @@ __device__ double fe_block_sum(double v, double* red) {
 __global__ void __launch_bounds__(256) fe_residual_kernel(long long total, const double* __restrict__ u,
                                                           const double* __restrict__ f,
                                                           const unsigned char* __restrict__ flags,
-                                                          const double* __restrict__ y, double* acc) {
+                                                          const double* __restrict__ y, double* acc,
+                                                          double* __restrict__ rvec) {
   __shared__ double red[32];
   double r2 = 0.0, f2 = 0.0;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
@@ -166,6 +167,7 @@ __global__ void __launch_bounds__(256) fe_residual_kernel(long long total, const
       const double ku = (fl & (1 << c)) ? u[2 * t + c] : y[2 * t + c];
       const double r = fv - ku;
       r2 += r * r;
+      if (rvec) rvec[2 * t + c] = r;
     }
   }
   r2 = fe_block_sum(r2, red);
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__(256) fe_residual_kernel(long long total, const
 __global__ void fe_group_residual_kernel(double gamma, int ngroups, const int* gstart, const long long* gidx,
                                          const double* __restrict__ u, const double* __restrict__ f,
                                          const unsigned char* __restrict__ flags, const double* __restrict__ y,
-                                         double* acc) {
+                                         double* acc, double* __restrict__ rvec) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   double r2 = 0.0;
   if (g < ngroups) {
@@ -200,6 +202,7 @@ __global__ void fe_group_residual_kernel(double gamma, int ngroups, const int* g
         const double row = fixed ? uv : sy + gamma * (cnt * uv - su);
         const double r = f[2 * v + c] - row;
         r2 += r * r;
+        if (rvec) rvec[2 * v + c] = r;
       }
     }
   }
@@ -317,10 +320,12 @@ void fe_apply(cudaStream_t s, const qtt_tensor* K, const double* x, double* y) {
   QTT_CHECK_LAUNCH();
 }
 
+namespace {
 // ||f - K (u + u2)|| / ||f|| (u2 may be NULL) with K applied as the
-// assembled finite-element operator
-double residual_fe(cudaStream_t s, const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* u2,
-                   const qtt_tensor* f) {
+// assembled finite-element operator; rvec (NULL, or 2 q 4^L doubles on the
+// device) receives the residual vector in canonical order
+double residual_fe_impl(cudaStream_t s, Arena& ar, const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* u2,
+                        const qtt_tensor* f, double* rvec) {
   QTT_REQUIRE(has_fe_operator(K), "residual: K does not come from qtt_assemble_stiffness");
   const FeOperator& op = *K->fe;
   QTT_REQUIRE(op.q >= 1 && op.q <= 16, "residual: patch count out of range");
@@ -335,7 +340,6 @@ double residual_fe(cudaStream_t s, const qtt_tensor* K, const qtt_tensor* u, con
   p.gamma = op.gamma;
   element_matrix(op.E, op.nu, 1.0 / (n - 1.0), p.Ke);
   for (int i = 0; i < 4 * op.q; ++i) p.bc[i] = op.bc[i];
-  Arena ar(s);
   double* uf = ar.alloc<double>(2 * total);
   double* ff = ar.alloc<double>(2 * total);
   double* y = ar.alloc<double>(2 * total);
@@ -366,17 +370,41 @@ double residual_fe(cudaStream_t s, const qtt_tensor* K, const qtt_tensor* u, con
   fe_stencil_kernel<<<grid_for_n(total, 8), 256, 0, s>>>(p, uf, flags, y);
   QTT_CHECK_LAUNCH();
   QTT_CUDA(cudaMemsetAsync(acc, 0, 2 * sizeof(double), s));
-  fe_residual_kernel<<<grid_for_n(total, 4), 256, 0, s>>>(total, uf, ff, flags, y, acc);
+  fe_residual_kernel<<<grid_for_n(total, 4), 256, 0, s>>>(total, uf, ff, flags, y, acc, rvec);
   QTT_CHECK_LAUNCH();
   if (ngroups > 0) {
     fe_group_residual_kernel<<<(ngroups + 127) / 128, 128, 0, s>>>(op.gamma, ngroups, d_start, d_idx, uf, ff, flags,
-                                                                   y, acc);
+                                                                   y, acc, rvec);
     QTT_CHECK_LAUNCH();
   }
   double h[2] = {0.0, 0.0};
   QTT_CUDA(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
   QTT_CUDA(cudaStreamSynchronize(s));
   return h[1] > 0 ? std::sqrt(h[0] / h[1]) : std::sqrt(h[0]);
+}
+}  // namespace
+
+double residual_fe(cudaStream_t s, const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* u2,
+                   const qtt_tensor* f) {
+  Arena ar(s);
+  return residual_fe_impl(s, ar, K, u, u2, f, nullptr);
+}
+
+// f - K u formed element by element in FP64 (the assembled operator, as in
+// residual_fe), reordered to QTT order and compressed by TT-SVD at relative
+// accuracy eps with ranks <= max_rank; *rel = ||f - K u|| / ||f||.
+qtt_tensor* residual_fe_tt(cudaStream_t s, const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* f, double eps,
+                           int max_rank, double* rel) {
+  QTT_REQUIRE(has_fe_operator(K), "residual: K does not come from qtt_assemble_stiffness");
+  const FeOperator& op = *K->fe;
+  const long long total = 2LL * op.q << (2 * op.L);
+  Arena ar(s);
+  double* rc = ar.alloc<double>(total);
+  const double r = residual_fe_impl(s, ar, K, u, nullptr, f, rc);
+  if (rel) *rel = r;
+  double* rz = ar.alloc<double>(total);
+  from_canonical<double>(s, rc, rz, op.L, op.q);
+  return tt_svd_full(s, ar, rz, f->d, f->n, eps, max_rank);
 }
 
 }  // namespace qtt
@@ -412,6 +440,29 @@ extern "C" int qtt_residual_fe(const qtt_tensor* K, const qtt_tensor* u, const q
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     qtt::StreamScope scope_(s);
     *out = qtt::residual_fe(s, K, u, nullptr, f);
+    return QTT_OK;
+  } catch (const qtt::QttError& e) {
+    qtt::set_last_error(e.what());
+    return e.code;
+  } catch (const std::exception& e) {
+    qtt::set_last_error(e.what());
+    return QTT_EINVAL;
+  }
+}
+
+extern "C" int qtt_residual_fe_tt(const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* f, double eps,
+                                  int max_rank, qtt_tensor** r, double* rel, void* stream) {
+  try {
+    QTT_REQUIRE(K && u && f && r, "qtt_residual_fe_tt: null argument");
+    QTT_REQUIRE(K->is_matrix && !u->is_matrix && !f->is_matrix && K->d == u->d && K->d == f->d,
+                "qtt_residual_fe_tt: K must be an MPO and u, f MPS of equal length");
+    for (int k = 0; k < K->d; ++k)
+      QTT_REQUIRE(K->n[k] == u->n[k] && K->n[k] == f->n[k], "qtt_residual_fe_tt: mode sizes differ");
+    QTT_REQUIRE(eps >= 1e-6 && eps < 1.0, "qtt_residual_fe_tt: eps must lie in [1e-6, 1)");
+    QTT_REQUIRE(max_rank >= 1, "qtt_residual_fe_tt: max_rank must be positive");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    qtt::StreamScope scope_(s);
+    *r = qtt::residual_fe_tt(s, K, u, f, eps, max_rank, rel);
     return QTT_OK;
   } catch (const qtt::QttError& e) {
     qtt::set_last_error(e.what());

@@ -201,7 +201,28 @@ __global__ void canonical_scatter_kernel(const T* __restrict__ in, T* __restrict
     out[o] = in[zorder_dev(i, j, L) + nn * m + nn * q * c];
   }
 }
+
+// the inverse reordering: canonical -> QTT order
+template <typename T>
+__global__ void canonical_gather_kernel(const T* __restrict__ in, T* __restrict__ out, int L, int q, long long total) {
+  const long long n = 1LL << L, nn = n * n;
+  for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < total;
+       o += (long long)gridDim.x * blockDim.x) {
+    int c = (int)(o & 1);
+    long long node = (o >> 1) % nn;
+    long long m = (o >> 1) / nn;
+    long long i = node % n, j = node / n;
+    out[zorder_dev(i, j, L) + nn * m + nn * q * c] = in[o];
+  }
+}
 }  // namespace
+
+template <typename T>
+void from_canonical(cudaStream_t s, const T* in, T* out, int L, int q) {
+  const long long total = 2LL * q << (2 * L);
+  canonical_gather_kernel<T><<<grid_for(total), 256, 0, s>>>(in, out, L, q, total);
+  QTT_CHECK_LAUNCH();
+}
 
 template <typename T>
 void core_product(cudaStream_t s, int R0, int n, int mm, int R1, int r0, int p, int r1, const T* A, const T* X, T* Y) {
@@ -480,6 +501,101 @@ int round_tt(cudaStream_t s, Arena& ar, qtt_tensor* x, double tol, int max_rank)
 }
 
 namespace {
+// B (rows x cols, ld rows) = diag(S) A[0:rows, :] (A with leading dimension lda)
+__global__ void scale_rows_kernel(int rows, long long cols, const double* __restrict__ A, int lda,
+                                  const double* __restrict__ S, double* __restrict__ B) {
+  const long long total = (long long)rows * cols;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % rows);
+    const long long j = t / rows;
+    B[t] = S[i] * A[i + j * lda];
+  }
+}
+}  // namespace
+
+// Left-to-right TT-SVD of a full FP64 vector (QTT order).  The unfolding
+// C_k (rows = r_{k-1} n_k, cols = the remaining index range) is truncated
+// through the eigendecomposition of its Gram matrix C_k C_k^T when it is
+// wide (the Gram product is one split-K GEMM, where a Householder QR of the
+// transposed C_k would run single-CTA panels over millions of rows), and
+// through its SVD when it is tall.  The eigenvalues are the squared
+// singular values; the kept eigenvectors, those of singular values above
+// the truncation level delta = eps ||v|| / sqrt(d - 1), carry a relative
+// error of about 1e-16 (sigma_1 / sigma_k)^2, which suits tolerances
+// eps >= 1e-6.  The discarded tail of every unfolding is <= delta.
+qtt_tensor* tt_svd_full(cudaStream_t s, Arena& ar, const double* v, int d, const int* n, double eps, int max_rank) {
+  QTT_REQUIRE(d >= 1 && v && n, "tt_svd_full: bad arguments");
+  long long total = 1;
+  for (int k = 0; k < d; ++k) total *= n[k];
+  std::vector<int> r(d + 1, 1), ones(d, 1);
+  std::vector<const double*> core(d, nullptr);
+  const double* C = v;
+  long long cols = total;
+  int rprev = 1;
+  double delta = -1.0;
+  for (int k = 0; k < d - 1; ++k) {
+    const int rows = rprev * n[k];
+    cols /= n[k];
+    QTT_REQUIRE(cols <= 2147483647LL, "tt_svd_full: unfolding too large");
+    const int kk = (int)std::min<long long>(rows, cols);
+    double* U = ar.alloc<double>((size_t)rows * kk);
+    double* S = ar.alloc<double>(kk);
+    std::vector<double> sv(kk);
+    double* Vt = nullptr;   // tall case: the right factor
+    if (cols > rows) {
+      double* G = ar.alloc<double>((size_t)rows * rows);
+      gemm<double>(s, false, true, rows, rows, (int)cols, 1.0, C, rows, 0, C, rows, 0, 0.0, G, rows, 0);
+      double* Vg = ar.alloc<double>((size_t)rows * rows);
+      svd<double>(s, ar, rows, rows, G, rows, U, rows, S, Vg, rows);
+      QTT_CUDA(cudaMemcpyAsync(sv.data(), S, sizeof(double) * kk, cudaMemcpyDeviceToHost, s));
+      QTT_CUDA(cudaStreamSynchronize(s));
+      for (double& x : sv) x = std::sqrt(std::max(0.0, x));
+    } else {
+      double* A = ar.alloc<double>((size_t)rows * cols);
+      QTT_CUDA(cudaMemcpyAsync(A, C, sizeof(double) * rows * cols, cudaMemcpyDeviceToDevice, s));
+      Vt = ar.alloc<double>((size_t)kk * cols);
+      svd<double>(s, ar, rows, (int)cols, A, rows, U, rows, S, Vt, kk);
+      QTT_CUDA(cudaMemcpyAsync(sv.data(), S, sizeof(double) * kk, cudaMemcpyDeviceToHost, s));
+      QTT_CUDA(cudaStreamSynchronize(s));
+    }
+    if (delta < 0.0) {
+      double nrm2 = 0.0;
+      for (double x : sv) nrm2 += x * x;
+      delta = eps * std::sqrt(nrm2) / std::sqrt((double)std::max(1, d - 1));
+    }
+    const int rk = std::max(1, truncation_rank(sv, delta, max_rank, nullptr));
+    double* Uk = ar.alloc<double>((size_t)rows * rk);
+    copy2d<double>(s, rows, rk, U, rows, Uk, rows);
+    core[k] = Uk;
+    double* Cn = ar.alloc<double>((size_t)rk * cols);
+    if (Vt) {
+      // C_{k+1} = diag(S_k) Vt_k (leading rk rows)
+      scale_rows_kernel<<<grid_for((long long)rk * cols), 256, 0, s>>>(rk, cols, Vt, kk, S, Cn);
+      QTT_CHECK_LAUNCH();
+    } else {
+      // C_{k+1} = U_k^T C_k, in column blocks that keep the GEMM grid's
+      // second dimension within its limit
+      constexpr long long kBlock = 1LL << 20;
+      for (long long c0 = 0; c0 < cols; c0 += kBlock) {
+        const int nc = (int)std::min(kBlock, cols - c0);
+        gemm<double>(s, true, false, rk, nc, rows, 1.0, Uk, rows, 0, C + c0 * rows, rows, 0, 0.0, Cn + c0 * rk, rk,
+                     0);
+      }
+    }
+    C = Cn;
+    rprev = rk;
+    r[k + 1] = rk;
+  }
+  core[d - 1] = C;
+  qtt_tensor* t = tensor_alloc(d, n, ones.data(), r.data(), QTT_F64, 0);
+  for (int k = 0; k < d; ++k)
+    QTT_CUDA(cudaMemcpyAsync(t->core[k], core[k], sizeof(double) * (size_t)r[k] * n[k] * r[k + 1],
+                             cudaMemcpyDeviceToDevice, s));
+  return t;
+}
+
+namespace {
 template <typename T>
 __global__ void scale_columns_kernel(int rows, int cols, const T* __restrict__ A, int lda, const T* __restrict__ S,
                                      T* __restrict__ B, int ldb) {
@@ -508,7 +624,8 @@ void scale_columns(cudaStream_t s, int rows, int cols, const T* A, int lda, cons
   template void right_orthogonalize<T>(cudaStream_t, Arena&, qtt_tensor*, int);                                  \
   template double norm<T>(cudaStream_t, Arena&, const qtt_tensor*);                                              \
   template int round_tt<T>(cudaStream_t, Arena&, qtt_tensor*, double, int);                                      \
-  template void scale_columns<T>(cudaStream_t, int, int, const T*, int, const T*, T*, int);
+  template void scale_columns<T>(cudaStream_t, int, int, const T*, int, const T*, T*, int);                    \
+  template void from_canonical<T>(cudaStream_t, const T*, T*, int, int);
 QTT_INST_TT(double)
 QTT_INST_TT(float)
 

@@ -44,6 +44,18 @@ int round_tt(cudaStream_t s, Arena& ar, qtt_tensor* x, double tol, int max_rank)
 qtt_tensor* round_residual_rand(cudaStream_t s, const qtt_tensor* K, const qtt_tensor* u, const qtt_tensor* f,
                                 int ell, unsigned long long seed, double* kept_norm);
 
+// canonical full vector (patch blocks of interleaved components
+// 2 (i + n j) + c, 2 q 4^L entries) -> QTT (Z-block) order
+template <typename T>
+void from_canonical(cudaStream_t s, const T* in, T* out, int L, int q);
+
+// TT-SVD of a full FP64 device vector in QTT order (first core's index
+// fastest) with mode sizes n[0..d): new left-orthonormal tensor whose every
+// unfolding drops a tail <= eps ||v|| / sqrt(d - 1), ranks capped at
+// max_rank (> 0); meant for eps >= 1e-6 (Gram eigendecomposition of wide
+// unfoldings)
+qtt_tensor* tt_svd_full(cudaStream_t s, Arena& ar, const double* v, int d, const int* n, double eps, int max_rank);
+
 // B = A diag(S)
 template <typename T>
 void scale_columns(cudaStream_t s, int rows, int cols, const T* A, int lda, const T* S, T* B, int ldb);

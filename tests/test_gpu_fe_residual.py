@@ -81,3 +81,40 @@ def test_fe_residual_refuses_a_rounded_operator():
     with pytest.raises(q.QttError) as e:
         q.qtt_residual_fe(K, u, f)
     assert e.value.code == _lib.QTT_EINVAL
+
+
+@pytest.mark.parametrize("make,args", PROBLEMS)
+def test_fe_residual_tt_matches_oracle_vector(make, args):
+    """qtt_residual_fe_tt: the QTT residual expanded back equals the oracle's
+    f - K u (masked duplicated system, QTT order) within the TT-SVD bound
+    eps ||r||, its ranks respect the cap, and rel is the stencil residual."""
+    prob = make(*args)
+    K, f = q.qtt_assemble_stiffness(prob)
+    modes = W.qtt_modes(prob)
+    u = q.QTT.from_cores(W.random_tt(44, modes, [1] + [4] * (len(modes) - 1) + [1]))
+    Ko, fo, _ = fem.duplicated_system(prob, masked=True)
+    r_or = fo - Ko @ q.qtt_to_full(u).cpu().numpy()
+    eps = 1e-5
+    r, rel = q.qtt_residual_fe_tt(K, u, f, eps=eps, max_rank=512)
+    got = q.qtt_to_full(r).cpu().numpy()
+    assert np.linalg.norm(got - r_or) <= 2 * eps * np.linalg.norm(r_or)
+    assert abs(rel - np.linalg.norm(r_or) / np.linalg.norm(fo)) <= 1e-11 * rel
+    r4, _ = q.qtt_residual_fe_tt(K, u, f, eps=eps, max_rank=4)
+    assert max(r4.ranks) <= 4
+
+
+def test_fe_residual_tt_keeps_the_error_carrying_part():
+    """Near the solution the residual is dominated by high-frequency parts
+    whose image under K^-1 is small; the compressed residual at eps = 1e-3
+    must keep K^-1 r (what an outer correction solves for) to within 5 %."""
+    import scipy.sparse.linalg as spla
+    prob = W.plate_traction_smooth(6)
+    K, f = q.qtt_assemble_stiffness(prob)
+    u, info = q.qtt_solve(K, f, tol=1e-9, max_sweeps=30, refine_max=-1)
+    Ko, fo, _ = fem.duplicated_system(prob, masked=True)
+    lu = spla.splu(Ko.tocsc())
+    r_or = fo - Ko @ q.qtt_to_full(u).cpu().numpy()
+    r, _ = q.qtt_residual_fe_tt(K, u, f, eps=1e-3, max_rank=128)
+    e_or = lu.solve(r_or)
+    e_tt = lu.solve(q.qtt_to_full(r).cpu().numpy())
+    assert np.linalg.norm(e_tt - e_or) <= 0.05 * np.linalg.norm(e_or)
