@@ -271,8 +271,9 @@ typedef struct {
  * iterative refinement: the residual f - K u is formed in FP64 and
  * compressed -- element by element and TT-SVD-rounded (qtt_residual_fe_tt,
  * rank <= 128) when K comes from qtt_assemble_stiffness and the relative
- * residual is below 1e-9, where forming it inside the QTT cores loses its
- * low-frequency part to cancellation; otherwise by the QTT matvec with
+ * residual is below 1e-9 (or a correction has failed to halve it), where
+ * forming it inside the QTT cores loses its low-frequency part to
+ * cancellation; otherwise by the QTT matvec with
  * randomized FP64 rounding (qtt_round_residual) -- K d = r is solved the
  * same way to inner_tol, and u <- round(u + d).  QTT_F32 runs everything in
  * FP32 without refinement.  Creates *x; info may be NULL.  Returns

@@ -40,7 +40,8 @@ qtt_tensor* residual_fe_tt(cudaStream_t s, const qtt_tensor* K, const qtt_tensor
                            int max_rank, double* rel);
 // The refinement forms its residual element by element (TT-SVD, ranks
 // <= kFeResidualRank) once the FP64 relative residual is below
-// kFeResidualBelow.  Measured: on the L = 10 plate at 5e-10 the residual
+// kFeResidualBelow, or once a correction from the QTT-formed residual has
+// failed to halve the residual.  Measured: on the L = 10 plate at 5e-10 the residual
 // formed in QTT arithmetic kept 4 % of K^-1 r, the element-by-element one
 // (rank 128) kept it all and six refinements took the error against sparse
 // direct from 5.2e-9 to 7e-10; on the L = 12 plates at 2-7e-8 the QTT
@@ -1410,7 +1411,8 @@ int solve(const qtt_tensor* K, const qtt_tensor* f, const qtt_tensor* x0, const 
     Tptr u = x0 ? own(tensor_clone(x0, QTT_F64, s)) : default_x0(s, f, QTT_F64);
     Tptr z = z0 ? own(tensor_clone(z0, QTT_F64, s)) : default_z0(s, f, rho, QTT_F64);
     rc = amen_run<double>(s, K, f, u.get(), z.get(), o.tol, o, inf, mixed, refine_max > 0);
-    double fnorm = -1.0;
+    double fnorm = -1.0, prev_rel = -1.0;
+    bool qtt_residual_stalled = false;
     for (int it = 0;; ++it) {
       // a passing in-sweep check stops the sweeps at once, so a stored value
       // <= tol is the final iterate's residual; otherwise measure it now
@@ -1418,6 +1420,10 @@ int solve(const qtt_tensor* K, const qtt_tensor* f, const qtt_tensor* x0, const 
                              ? inf->rel_residual
                              : timed_residual64(s, K, u.get(), f, inf);
       inf->rel_residual = rel;
+      // a correction that did not halve the residual: the residual formed
+      // in QTT arithmetic has lost what the correction needs
+      if (prev_rel > 0.0 && rel > 0.5 * prev_rel) qtt_residual_stalled = true;
+      prev_rel = rel;
       if (o.verbose) fprintf(stderr, "[qtt_solve] check %d: FP64 rel residual %.3e\n", it, rel);
       if (rel <= o.tol || it >= refine_max) {
         rc = rel <= o.tol ? QTT_OK : QTT_ENOCONV;
@@ -1429,7 +1435,7 @@ int solve(const qtt_tensor* K, const qtt_tensor* f, const qtt_tensor* x0, const 
         fnorm = norm<double>(s, ar, f);
       }
       Tptr r = own(nullptr);
-      if (has_fe_operator(K) && rel <= kFeResidualBelow) {
+      if (has_fe_operator(K) && (rel <= kFeResidualBelow || qtt_residual_stalled)) {
         // Near the FP64 floor the residual's low-frequency part -- the one
         // that carries the error, K^-1 r -- is a small fraction of ||r||
         // and lost to cancellation when f - K u is formed inside the QTT
