@@ -264,6 +264,8 @@ __global__ void jacobi_coop_kernel(int m, int n, T* W, int ldw, T* Vm, int ldv, 
   // 1e-8 in FP64) leaves the columns orthogonal to working accuracy
   // (quadratic convergence), so it ends the sweeps without a confirming one
   const Acc big = (sizeof(T) == 8) ? (Acc)1e-8 : (Acc)1e-4;
+  constexpr int JT = 8;                       // register path: columns of <= 256 rows
+  const bool inreg = m <= 32 * JT && n <= 32 * JT;
   for (; sweep < max_sweeps; ++sweep) {
     bool any = false, large = false;
     for (int round = 0; round < np - 1; ++round) {
@@ -280,7 +282,50 @@ __global__ void jacobi_coop_kernel(int m, int n, T* W, int ldw, T* Vm, int ldv, 
         if (q >= n) continue;
         T* wp = W + (long long)p * ldw;
         T* wq = W + (long long)q * ldw;
+        T* vp = Vm + (long long)p * ldv;
+        T* vq = Vm + (long long)q * ldv;
         Acc al = 0, be = 0, ga = 0;
+        if (inreg) {
+          // the pair's four columns in registers: every load of the round
+          // is issued at once, and the rotation reuses the loaded values
+          Acc a[JT], b[JT], va[JT], vb[JT];
+#pragma unroll
+          for (int t = 0; t < JT; ++t) {
+            const int i = lane + 32 * t;
+            a[t] = i < m ? (Acc)__ldcg(wp + i) : (Acc)0;
+            b[t] = i < m ? (Acc)__ldcg(wq + i) : (Acc)0;
+            va[t] = i < n ? (Acc)__ldcg(vp + i) : (Acc)0;
+            vb[t] = i < n ? (Acc)__ldcg(vq + i) : (Acc)0;
+          }
+#pragma unroll
+          for (int t = 0; t < JT; ++t) {
+            al += a[t] * a[t];
+            be += b[t] * b[t];
+            ga += a[t] * b[t];
+          }
+          al = wsum(al);
+          be = wsum(be);
+          ga = wsum(ga);
+          if (ga == (Acc)0 || !(fabs(ga) > tolf * sqrt(al * be))) continue;
+          if (fabs(ga) > big * sqrt(al * be)) large = true;
+          Acc zeta = (be - al) / ((Acc)2 * ga);
+          Acc t = (zeta >= (Acc)0 ? (Acc)1 : (Acc)-1) / (fabs(zeta) + sqrt((Acc)1 + zeta * zeta));
+          Acc cs = (Acc)1 / sqrt((Acc)1 + t * t), sn = cs * t;
+#pragma unroll
+          for (int u = 0; u < JT; ++u) {
+            const int i = lane + 32 * u;
+            if (i < m) {
+              wp[i] = (T)(cs * a[u] - sn * b[u]);
+              wq[i] = (T)(sn * a[u] + cs * b[u]);
+            }
+            if (i < n) {
+              vp[i] = (T)(cs * va[u] - sn * vb[u]);
+              vq[i] = (T)(sn * va[u] + cs * vb[u]);
+            }
+          }
+          any = true;
+          continue;
+        }
         for (int i = lane; i < m; i += 32) {
           Acc a = __ldcg(wp + i), b = __ldcg(wq + i);
           al += a * a;
@@ -300,8 +345,6 @@ __global__ void jacobi_coop_kernel(int m, int n, T* W, int ldw, T* Vm, int ldv, 
           wp[i] = (T)(cs * a - sn * b);
           wq[i] = (T)(sn * a + cs * b);
         }
-        T* vp = Vm + (long long)p * ldv;
-        T* vq = Vm + (long long)q * ldv;
         for (int i = lane; i < n; i += 32) {
           Acc a = __ldcg(vp + i), b = __ldcg(vq + i);
           vp[i] = (T)(cs * a - sn * b);
